@@ -1,0 +1,290 @@
+"""Benchmark: chemistry cell-steps/s of the bulk-sparse GPU integrator on one flow step.
+
+Workload (one step = one chemistry sub-step of the whole field): a 128^3 reacting-sheet field
+(2,097,152 cells, 5% of them in a curved reacting sheet at 1500-3000 K with Dirichlet(0.5)
+composition, the rest cold premix at 300-400 K), the seeded H2-air-shaped mechanism (9 species,
+21 reversible reactions), dt = 1e-8 s, FP32 state.  Each step restores the input state from a
+pristine device copy, flushes L2 (256 MiB write) and advances every cell through the C ABI
+(bulk kernel + stiff kernel).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
+
+Under torchrun (N > 1) every rank advances its own field (seed = rank): weak scaling, no
+collective on the data path; the step time is the max over ranks.  `--impl reference` times the
+FP64 CPU oracle (the checker of this library) on bounded stratified samples of the same field.
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "chem cell-steps/s at rel err ≤1e-4 (gated surrogate vs plain GPU), % roofline"
+UNIT = "cell-steps/s"
+DT = 1e-8
+N_EDGE = 128
+NS = 9
+# algorithmic FP64 flops of the stiff integrator per unit of work (n = 9 species):
+#   per attempted step: iteration matrix I - g h J (2 n^2) + LU with partial pivoting
+#       (sum_k 2 (n-k-1)^2 + (n-k-1), plus n reciprocals) + error filter (5 n + 2 n^2 + 2 n)
+#   per Newton iteration: T(e) (mixture 12 n + 2 iterations x 21) + residual 3 n + solve 2 n^2
+#       + update/norm 2 n
+#   per accepted step: T(e) of the new state (12 n + 42)
+F_ATTEMPT = 2 * NS * NS + sum(2 * (NS - k - 1) ** 2 + (NS - k - 1) for k in range(NS)) + NS \
+    + 5 * NS + 2 * NS * NS + 2 * NS
+F_NEWTON = (12 * NS + 42) + 3 * NS + 2 * NS * NS + 2 * NS
+F_ACCEPT = 12 * NS + 42
+# FP64 peak derived from the unit count: 152 SMs x 2 FP64 FMA lanes/clock x 2 flops x 2.07 GHz
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+def _config(n, args):
+    return {"workload": f"reacting sheet {N_EDGE}^3 ({n} cells, 5% reacting), H2-air-shaped mechanism "
+                        f"9 species / 21 reactions, dt = {DT:g} s, FP32 state, bulk-sparse",
+            "cells": n, "dt_s": DT, "rtol": args.rtol, "atol": args.atol,
+            "l2": "flushed (256 MiB write) and state restored from a pristine copy inside every step",
+            "mechanism_seed": 0, "field_seed": "rank"}
+
+
+def _field(seed):
+    mech = synth.h2_air_mechanism(0)
+    T, p, Y, hot = synth.sheet_field(mech, n=N_EDGE, seed=seed)
+    return mech, T.astype(np.float32), p.astype(np.float32), np.ascontiguousarray(Y, dtype=np.float32), hot
+
+
+def _oracle_sample(mech, T, p, Y, hot, n_sample, seed):
+    import oracle
+    idx = synth.stratified_sample(hot, n_sample, seed=seed)
+    rho, e = oracle.state_from_TpY(mech, T[idx], p[idx], Y[:, idx])
+    rho, e = rho.astype(np.float32), e.astype(np.float32)
+    t0 = time.perf_counter()
+    T1, _, Y1, steps = oracle.advance(mech, rho, e, T[idx], Y[:, idx], DT)
+    wall = time.perf_counter() - t0
+    return idx, rho, e, T1, Y1, wall, oracle.max_threads()
+
+
+class ClockSampler:
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.path = None
+        try:
+            self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={CLOCK_QUERY}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(gpu_index)], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.count(",") >= 8]
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[j] for r in rows for j in range(4) if "Active" in r[5 + j] and "Not" not in r[5 + j]})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def run_gpu(args, rank, world, local_rank, dist):
+    import torch
+    import paper_2510_23993_gb300 as chem
+    chem.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    mech, T, p, Y, hot = _field(seed=rank)
+    n = T.size
+    ctx = chem.Context(mech, max_cells=n, rtol=args.rtol, atol=args.atol, flags=chem.CHEM_FLAG_TIMING)
+    tT, tp, tY = (torch.from_numpy(a).to(dev) for a in (T, p, Y))
+    rho, e = torch.empty_like(tT), torch.empty_like(tT)
+    ctx.state_from_TpY(tT, tp, tY, rho, e)
+    T0, Y0 = tT.clone(), tY.clone()
+    sub = torch.zeros(n, dtype=torch.int32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step(i):
+        tT.copy_(T0)
+        tY.copy_(Y0)
+        flush.fill_(i & 0xFF)
+        ctx.advance(tT, tp, tY, rho, e, DT, sub)
+        return ctx.status()
+
+    for i in range(args.warmup):
+        step(i)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local_rank)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    stats = [step(i) for i in range(args.steps)]
+    ev1.record()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    total_cells = n * world
+    value = total_cells * args.steps / (ms / 1e3)
+    for s in stats:
+        assert s["status"] == 0, s
+    # dominant kernel: the stiff kernel (FP64 pipe); its algorithmic FP64 work per launch
+    stiff_ms = float(np.mean([s["stiff_ms"] for s in stats]))
+    bulk_ms = float(np.mean([s["bulk_ms"] for s in stats]))
+    flops = float(np.mean([s["attempts"] * F_ATTEMPT + s["newton"] * F_NEWTON + s["substeps"] * F_ACCEPT
+                           for s in stats]))
+    achieved = flops / (stiff_ms / 1e3) / 1e12
+    roof = {"kernel": "stiff_kernel", "bound": "alu", "pipe": "fp64", "achieved": achieved,
+            "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+            "traffic": _traffic(), "kernel_ms": stiff_ms, "bulk_kernel_ms": bulk_ms,
+            "algorithmic_flops_per_launch": flops,
+            "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2.07 GHz (no FP64 figure in MEASURED_PEAKS.json)"}
+    # end to end through the host entry point (pinned host buffers, copies inside the timing)
+    e2e = None
+    if args.e2e:
+        hT, hp, hY = (torch.from_numpy(a).pin_memory() for a in (T, p, Y))
+        hrho, he = rho.cpu().pin_memory(), e.cpu().pin_memory()
+        hsub = torch.zeros(n, dtype=torch.int32).pin_memory()
+        wall = 0.0
+        for i in range(args.warmup + args.steps):
+            hT.copy_(torch.from_numpy(T))
+            hY.copy_(torch.from_numpy(Y))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ctx.advance_host(hT, hp, hY, hrho, he, DT, hsub)
+            if i >= args.warmup:
+                wall += time.perf_counter() - t0
+        if dist is not None:
+            t = torch.tensor([wall], dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            wall = float(t.item())
+        e2e = {"value": total_cells * args.steps / wall, "unit": UNIT,
+               "h2d_bytes_per_step": int(n * 4 * (NS + 4)), "d2h_bytes_per_step": int(n * 4 * (NS + 3))}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": _config(n, args), "roofline": roof, "e2e": e2e, "gpu_launches": 2 * args.steps * world,
+            "clocks": clk,
+            "stiff": {"queued_cells": stats[-1]["nqueued"], "bulk_cells": stats[-1]["nbulk"],
+                      "substeps_per_stiff_cell": stats[-1]["substeps"] / max(1, stats[-1]["nqueued"]),
+                      "newton_per_attempt": stats[-1]["newton"] / max(1, stats[-1]["attempts"])}}
+    if rank == 0 and world == 1 and args.cpu_baseline:
+        idx, orho, oe, oT, oY, wall, cores = _oracle_sample(mech, T, p, Y, hot, args.cpu_sample, seed=0)
+        line["cpu_baseline"] = {"value": len(idx) / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": f"{len(idx)} cells stratified from the same field "
+                                          f"({int(hot[idx].sum())} reacting), FP64 Radau IIA rtol 1e-10"}
+        line["accuracy"] = _accuracy(ctx, torch, dev, T[idx], p[idx], Y[:, idx], orho, oe, oT, oY)
+    return line
+
+
+def _accuracy(ctx, torch, dev, T, p, Y, rho, e, T_ref, Y_ref):
+    """Error of the GPU path against the oracle on the CPU-baseline sample (oracle inputs)."""
+    n = T.size
+    a = [torch.from_numpy(np.ascontiguousarray(x)).to(dev) for x in (T, p, Y, rho, e)]
+    s = torch.zeros(n, dtype=torch.int32, device=dev)
+    ctx.advance(a[0], a[1], a[2], a[3], a[4], DT, s)
+    ctx.status()
+    Tg, Yg = a[0].cpu().numpy().astype(np.float64), a[2].cpu().numpy().astype(np.float64)
+    big = Y_ref >= 1e-6
+    rel = np.where(big, np.abs(Yg - Y_ref) / np.maximum(Y_ref, 1e-300), 0.0)
+    ab = np.where(~big, np.abs(Yg - Y_ref), 0.0)
+    eT = np.abs(Tg - T_ref) / T_ref
+    over = (rel.max(0) > 1e-4) | (ab.max(0) > 1e-10) | (eT > 1e-4)
+    return {"cells": int(n), "max_rel_Y": float(rel.max()), "p999_rel_Y": float(np.percentile(rel.max(0), 99.9)),
+            "max_abs_small_Y": float(ab.max()), "max_rel_T": float(eT.max()), "cells_over_1e-4": int(over.sum())}
+
+
+def _traffic():
+    """DRAM bytes per launch of the stiff kernel from the committed ncu summary, if it was taken on
+    the current source of the kernel (else null)."""
+    path = os.path.join(ROOT, "profiles", "stiff_kernel_traffic.json")
+    if not os.path.exists(path):
+        return None
+    rec = json.load(open(path))
+    src = os.path.join(ROOT, "paper_2510_23993_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in ("stiff.cu", "chem_device.cuh"):
+        h.update(open(os.path.join(src, f), "rb").read())
+    return rec.get("bytes_per_launch") if rec.get("source_sha256") == h.hexdigest() else None
+
+
+def run_reference(args, world):
+    mech, T, p, Y, hot = _field(seed=0)
+    walls, ncell = [], 0
+    for i in range(args.warmup + args.steps):
+        idx, _, _, _, _, wall, cores = _oracle_sample(mech, T, p, Y, hot, args.ref_sample, seed=i)
+        if i >= args.warmup:
+            walls.append(wall)
+            ncell += len(idx)
+    total = sum(walls)
+    value = ncell / total
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": _config(T.size, args),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{args.ref_sample} cells per step, stratified (5% reacting) from the "
+                                       f"{N_EDGE}^3 field; FP64 Radau IIA rtol 1e-10"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--rtol", type=float, default=1e-5)
+    ap.add_argument("--atol", type=float, default=1e-10)
+    ap.add_argument("--cpu-sample", type=int, default=8192)
+    ap.add_argument("--ref-sample", type=int, default=8192)
+    ap.add_argument("--no-e2e", dest="e2e", action="store_false")
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args, world)), flush=True)
+        return
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    line = run_gpu(args, rank, world, local_rank, dist)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,167 @@
+/*
+ * chem.h -- C ABI of the GB300 (sm_103a) per-cell stiff-chemistry library (libchem.so).
+ *
+ * The library advances every cell of a reacting-flow field over one flow time step dt as a
+ * constant-volume, adiabatic 0-D reactor (arxiv 2510.23993, Sec. 2.1, Eq. 5: dY_k/dt =
+ * W_k omega_k / rho; temperature from the internal energy at fixed rho by Newton iteration),
+ * with the bulk-sparse strategy of Algorithm 3 (Sec. 3.2): every active cell takes one bulk
+ * step with an error test, and only the cells that fail are compacted into a device queue and
+ * substepped implicitly (an L-stable 3-stage SDIRK method of order 3 whose stages are solved by
+ * Newton iterations on a dense per-cell Jacobian, with embedded error control).  Rates use the
+ * matrix (log-concentration) form of the kinetics in FP32; the Newton LU/solve of stiff cells
+ * and the temperature inversion run in FP64.
+ *
+ * Conventions for every entry point:
+ *   - arrays are structure-of-arrays (Sec. 3.1): a field F of n cells is F[i], i < n; the mass
+ *     fractions are Y[k * ld + i] for species k < ns and cell i < n, with ld >= n;
+ *   - "device" pointers are CUDA device memory owned by the caller; "host" pointers are host
+ *     memory owned by the caller; the library never frees caller memory;
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream); work is enqueued
+ *     asynchronously, nothing synchronizes unless the entry point says so;
+ *   - the return value is CHEM_OK (0) or a negative CHEM_E* code; argument errors are detected
+ *     on the host before anything is enqueued; per-cell failures are reported through the
+ *     per-cell substep counts and the counters that chem_status returns.
+ * The library allocates device memory only in chem_init (tables and workspace sized by
+ * max_cells) and frees it in chem_destroy.
+ */
+#ifndef CHEM_H
+#define CHEM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define CHEM_OK 0
+#define CHEM_EINVAL (-1)       /* bad argument, or non-finite / non-physical input cells */
+#define CHEM_ENOMEM (-2)       /* n > max_cells, or a device allocation failed */
+#define CHEM_EMAXSTEPS (-3)    /* a stiff cell reached k_max substeps (its count is -1) */
+#define CHEM_ENOCONV (-4)      /* a stiff cell's Newton iteration / step size collapsed */
+#define CHEM_ECUDA (-5)        /* a CUDA runtime call failed */
+#define CHEM_EUNSUPPORTED (-6) /* mechanism shape without a compiled kernel (ns) */
+
+/* Opaque context: device copy of the mechanism tables and the stiff-cell workspace. */
+typedef struct chem_ctx chem_ctx;
+
+/* Reaction mechanism (host memory, read by chem_init only; SI units).
+ * Thermo per species: NASA-7 a1..a7 then T_lo, T_hi (cp/R = a1 + a2 T + ... + a5 T^4,
+ * h/R = a1 T + a2 T^2/2 + ... + a5 T^5/5 + a6, s/R = a1 ln T + ... + a5 T^4/4 + a7); outside
+ * [T_lo, T_hi] cp is held at its boundary value.  All species must share T_lo and T_hi.
+ * Rate constant k_f = A T^b exp(-Ea / (R T)); reverse k_r = k_f / K_c (Sec. 2.1). */
+typedef struct {
+  int32_t ns, nr;               /* species, reactions */
+  const double *W;              /* [ns] molar masses, kg/mol */
+  const double *thermo;         /* [ns][9] */
+  const int8_t *nu_f, *nu_r;    /* [nr][ns] reactant / product coefficients, 0..2 */
+  const double *A, *b, *Ea;     /* [nr] SI pre-exponential, temperature exponent, J/mol */
+  const uint8_t *reversible;    /* [nr] 0/1 */
+  const uint8_t *third_body;    /* [nr] 0/1: rate multiplied by [M] = sum_k eff_k C_k */
+  const double *eff;            /* [nr][ns] third-body efficiencies (read for third-body rows) */
+} chem_mechanism;
+
+/* Integration parameters (copied by chem_init; can be changed with chem_set_params). */
+typedef struct {
+  double rtol;       /* relative tolerance of the bulk test and of the stiff integrator */
+  double atol;       /* absolute tolerance on mass fractions */
+  double T_min;      /* activity threshold (Algorithm 2/3 T_reaction_min): T < T_min is skipped */
+  double bulk_frac;  /* max relative change of any Y_k in one bulk step (Sec. 2.1, 1-5%) */
+  double y_floor;    /* floor of |Y_k| in the relative-change rule */
+  int32_t k_bulk;    /* explicit bulk substeps attempted per cell (Algorithm 3 K_max, 1..5) */
+  int32_t k_max;     /* cap of implicit substeps per stiff cell (Algorithm 3, 1e5) */
+  int32_t flags;     /* CHEM_FLAG_* bits, 0 by default */
+} chem_params;
+
+/* chem_params.flags: evaluate the rates of the stiff integrator in FP64 (FP64 tables) instead of
+ * FP32 (a precision reference for the mixed-precision default; the Jacobian stays FP32). */
+#define CHEM_FLAG_FP64_RATES 1
+/* chem_params.flags: record CUDA events around the bulk and the stiff kernel of each advance call
+ * (on the call's stream); chem_status then reports their durations.  Not for graph capture. */
+#define CHEM_FLAG_TIMING 2
+
+/* Counters of the last advance call (see chem_status). */
+typedef struct {
+  int64_t ncell;      /* cells in the call */
+  int64_t nskipped;   /* T < T_min */
+  int64_t nbulk;      /* accepted by the bulk step */
+  int64_t nqueued;    /* compacted into the stiff queue */
+  int64_t nfailed;    /* stiff cells that hit k_max or whose step size collapsed */
+  int64_t ninvalid;   /* non-finite or non-physical inputs (count -1, state untouched) */
+  int64_t substeps;   /* total implicit substeps of the stiff cells */
+  int64_t attempts;   /* attempted implicit steps (accepted + rejected): Jacobian + LU each */
+  int64_t newton;     /* Newton iterations of the stage solves (rates + T(e) + solve each) */
+  int32_t status;     /* CHEM_OK or the most severe per-cell error code */
+  float bulk_ms;      /* bulk kernel duration (CHEM_FLAG_TIMING), else 0 */
+  float stiff_ms;     /* stiff kernel duration (CHEM_FLAG_TIMING), else 0 */
+} chem_stats;
+
+/* Defaults: rtol 1e-5, atol 1e-10, T_min 0, bulk_frac 0.05, y_floor 1e-10, k_bulk 1,
+ * k_max 100000, flags 0. */
+void chem_default_params(chem_params *out);
+
+/* Create a context for one mechanism on the current CUDA device.  Copies the mechanism into
+ * device tables and allocates the workspace of up to max_cells cells (stiff queue, counters).
+ * Returns CHEM_EINVAL for an inconsistent mechanism, CHEM_EUNSUPPORTED if no kernel is compiled
+ * for ns, CHEM_ENOMEM / CHEM_ECUDA on allocation failure.  *out is NULL on failure. */
+int chem_init(const chem_mechanism *mech, const chem_params *params, int64_t max_cells,
+              chem_ctx **out);
+
+/* Replace the integration parameters used by later calls. */
+int chem_set_params(chem_ctx *ctx, const chem_params *params);
+
+/* Free the context and its device memory (synchronizes the device). NULL is ignored. */
+void chem_destroy(chem_ctx *ctx);
+
+/* Advance n cells over dt (Sec. 2.1 Eq. 5; Algorithm 3), FP32 state.  Device pointers.
+ *   T[n]      in: temperature guess (K); out: temperature consistent with e and the new Y
+ *   p[n]      out: pressure rho R T sum_k Y_k / W_k (Pa); may be NULL
+ *   Y[ns*ld]  in/out: mass fractions, SoA with leading dimension ld
+ *   rho[n]    in: density (kg/m^3), e[n] in: mass-specific internal energy (J/kg), both constant
+ *   substeps[n] out: 0 skipped (T < T_min), k_bulk accepted by the bulk step, > k_bulk stiff
+ *             (k_bulk + implicit substeps), -1 invalid input or failed cell (state untouched)
+ * Cells that are skipped, invalid or failed keep T, p, Y unchanged.  Returns CHEM_ENOMEM if
+ * n > max_cells.  Asynchronous on `stream`; graph-capturable. */
+int chem_advance(chem_ctx *ctx, float *T, float *p, float *Y, int64_t ld, const float *rho,
+                 const float *e, int64_t n, double dt, int32_t *substeps, void *stream);
+
+/* Same as chem_advance with FP64 state arrays (state arithmetic of the bulk step and of the
+ * stiff solver in FP64; rates still FP32). */
+int chem_advance_f64(chem_ctx *ctx, double *T, double *p, double *Y, int64_t ld,
+                     const double *rho, const double *e, int64_t n, double dt,
+                     int32_t *substeps, void *stream);
+
+/* End-to-end variant of chem_advance on HOST buffers (same layout, ld = n): copies the inputs
+ * to the context's device staging buffers, advances, copies T, p, Y, substeps back, and
+ * synchronizes `stream`.  Host buffers should be pinned for full copy bandwidth. */
+int chem_advance_host(chem_ctx *ctx, float *T, float *p, float *Y, const float *rho,
+                      const float *e, int64_t n, double dt, int32_t *substeps, void *stream);
+
+/* Density and internal energy from (T, p, Y) (ideal gas; e = sum_k Y_k u_k(T)), computed in
+ * FP64 and rounded to the output type.  Device pointers; asynchronous. */
+int chem_state_from_TpY(chem_ctx *ctx, const float *T, const float *p, const float *Y,
+                        int64_t ld, int64_t n, float *rho, float *e, void *stream);
+int chem_state_from_TpY_f64(chem_ctx *ctx, const double *T, const double *p, const double *Y,
+                            int64_t ld, int64_t n, double *rho, double *e, void *stream);
+
+/* Temperature from internal energy at fixed Y (the FP64 Newton inversion used by the
+ * integrators; Sec. 2.1).  T[n] in: guess, out: solution.  Device pointers; asynchronous. */
+int chem_temperature(chem_ctx *ctx, const float *Y, int64_t ld, const float *e, int64_t n,
+                     float *T, void *stream);
+
+/* dY/dt of Eq. 5 at given (rho, T, Y), evaluated with the FP32 matrix-form kinetics of the
+ * integrators.  dYdt[ns*ld] out.  Device pointers; asynchronous. */
+int chem_rates(chem_ctx *ctx, const float *rho, const float *T, const float *Y, int64_t ld,
+               int64_t n, float *dYdt, void *stream);
+
+/* Synchronize `stream` and return the counters of the last advance call on this context. */
+int chem_status(chem_ctx *ctx, void *stream, chem_stats *out);
+
+/* Static description of a status code. */
+const char *chem_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CHEM_H */

@@ -1,0 +1,255 @@
+"""GB300-native per-cell stiff chemistry: Python binding of libchem.so (include/chem.h).
+
+The binding only marshals arguments: every step of the chemistry runs in the library's CUDA
+kernels.  Functions keep the C names (chem_init, chem_advance, ...); `Context` is a small
+convenience wrapper over them that accepts torch tensors.  Importing the package does not
+load the library; the first call does, and fails loudly if libchem.so was not built.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libchem.so")
+
+CHEM_OK = 0
+CHEM_EINVAL = -1
+CHEM_ENOMEM = -2
+CHEM_EMAXSTEPS = -3
+CHEM_ENOCONV = -4
+CHEM_ECUDA = -5
+CHEM_EUNSUPPORTED = -6
+CHEM_FLAG_FP64_RATES = 1
+CHEM_FLAG_TIMING = 2
+
+_P = ctypes.POINTER
+_c_void_p = ctypes.c_void_p
+
+
+class chem_mechanism(ctypes.Structure):
+    _fields_ = [("ns", ctypes.c_int32), ("nr", ctypes.c_int32),
+                ("W", _P(ctypes.c_double)), ("thermo", _P(ctypes.c_double)),
+                ("nu_f", _P(ctypes.c_int8)), ("nu_r", _P(ctypes.c_int8)),
+                ("A", _P(ctypes.c_double)), ("b", _P(ctypes.c_double)), ("Ea", _P(ctypes.c_double)),
+                ("reversible", _P(ctypes.c_uint8)), ("third_body", _P(ctypes.c_uint8)),
+                ("eff", _P(ctypes.c_double))]
+
+
+class chem_params(ctypes.Structure):
+    _fields_ = [("rtol", ctypes.c_double), ("atol", ctypes.c_double), ("T_min", ctypes.c_double),
+                ("bulk_frac", ctypes.c_double), ("y_floor", ctypes.c_double),
+                ("k_bulk", ctypes.c_int32), ("k_max", ctypes.c_int32), ("flags", ctypes.c_int32)]
+
+
+class chem_stats(ctypes.Structure):
+    _fields_ = [("ncell", ctypes.c_int64), ("nskipped", ctypes.c_int64), ("nbulk", ctypes.c_int64),
+                ("nqueued", ctypes.c_int64), ("nfailed", ctypes.c_int64), ("ninvalid", ctypes.c_int64),
+                ("substeps", ctypes.c_int64), ("attempts", ctypes.c_int64), ("newton", ctypes.c_int64),
+                ("status", ctypes.c_int32), ("bulk_ms", ctypes.c_float), ("stiff_ms", ctypes.c_float)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def build(force=False, verbose=False):
+    """Compile libchem.so for sm_103a (nvcc; see build_lib.py)."""
+    from . import build_lib
+    return build_lib.build(force=force, verbose=verbose)
+
+
+def lib():
+    """The loaded libchem.so; raises if it has not been built (no fallback path exists)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2510_23993_gb300.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i64, d, i32 = _c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_int32
+        L.chem_default_params.argtypes = [_P(chem_params)]
+        L.chem_default_params.restype = None
+        L.chem_init.argtypes = [_P(chem_mechanism), _P(chem_params), i64, _P(vp)]
+        L.chem_set_params.argtypes = [vp, _P(chem_params)]
+        L.chem_destroy.argtypes = [vp]
+        L.chem_destroy.restype = None
+        adv = [vp, vp, vp, vp, i64, vp, vp, i64, d, vp, vp]
+        L.chem_advance.argtypes = adv
+        L.chem_advance_f64.argtypes = adv
+        L.chem_advance_host.argtypes = [vp, vp, vp, vp, vp, vp, i64, d, vp, vp]
+        L.chem_state_from_TpY.argtypes = [vp, vp, vp, vp, i64, i64, vp, vp, vp]
+        L.chem_state_from_TpY_f64.argtypes = [vp, vp, vp, vp, i64, i64, vp, vp, vp]
+        L.chem_temperature.argtypes = [vp, vp, i64, vp, i64, vp, vp]
+        L.chem_rates.argtypes = [vp, vp, vp, vp, i64, i64, vp, vp]
+        L.chem_status.argtypes = [vp, vp, _P(chem_stats)]
+        L.chem_strerror.argtypes = [i32]
+        L.chem_strerror.restype = ctypes.c_char_p
+        for name in ("chem_init", "chem_set_params", "chem_advance", "chem_advance_f64", "chem_advance_host",
+                     "chem_state_from_TpY", "chem_state_from_TpY_f64", "chem_temperature", "chem_rates",
+                     "chem_status"):
+            getattr(L, name).restype = i32
+        _lib = L
+    return _lib
+
+
+class ChemError(RuntimeError):
+    def __init__(self, code, what):
+        self.code = code
+        super().__init__(f"{what}: {lib().chem_strerror(code).decode()} ({code})")
+
+
+def _check(code, what):
+    if code != CHEM_OK:
+        raise ChemError(code, what)
+
+
+class Mechanism:
+    """Host copy of a mechanism dict (synth layout) as the C struct chem_mechanism."""
+
+    def __init__(self, mech):
+        self.ns, self.nr = int(mech["ns"]), int(mech["nr"])
+        self._keep = dict(
+            W=np.ascontiguousarray(mech["W"], np.float64),
+            thermo=np.ascontiguousarray(mech["thermo"], np.float64),
+            nu_f=np.ascontiguousarray(mech["nu_f"], np.int8),
+            nu_r=np.ascontiguousarray(mech["nu_r"], np.int8),
+            A=np.ascontiguousarray(mech["A"], np.float64),
+            b=np.ascontiguousarray(mech["b"], np.float64),
+            Ea=np.ascontiguousarray(mech["Ea"], np.float64),
+            reversible=np.ascontiguousarray(mech["reversible"], np.uint8),
+            third_body=np.ascontiguousarray(mech["third_body"], np.uint8),
+            eff=np.ascontiguousarray(mech["eff"], np.float64))
+        k = self._keep
+        ptr = lambda a, t: a.ctypes.data_as(_P(t))
+        self.c = chem_mechanism(self.ns, self.nr, ptr(k["W"], ctypes.c_double), ptr(k["thermo"], ctypes.c_double),
+                                ptr(k["nu_f"], ctypes.c_int8), ptr(k["nu_r"], ctypes.c_int8),
+                                ptr(k["A"], ctypes.c_double), ptr(k["b"], ctypes.c_double),
+                                ptr(k["Ea"], ctypes.c_double), ptr(k["reversible"], ctypes.c_uint8),
+                                ptr(k["third_body"], ctypes.c_uint8), ptr(k["eff"], ctypes.c_double))
+
+
+def chem_default_params(**overrides):
+    p = chem_params()
+    lib().chem_default_params(ctypes.byref(p))
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+def chem_init(mech, params=None, max_cells=0):
+    m = mech if isinstance(mech, Mechanism) else Mechanism(mech)
+    h = _c_void_p()
+    _check(lib().chem_init(ctypes.byref(m.c), ctypes.byref(params) if params is not None else None,
+                           int(max_cells), ctypes.byref(h)), "chem_init")
+    return h
+
+
+def chem_destroy(ctx):
+    lib().chem_destroy(ctx)
+
+
+def chem_set_params(ctx, params):
+    _check(lib().chem_set_params(ctx, ctypes.byref(params)), "chem_set_params")
+
+
+def _dp(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def chem_advance(ctx, T, p, Y, ld, rho, e, n, dt, substeps, stream=None):
+    fn = lib().chem_advance_f64 if T.dtype.itemsize == 8 else lib().chem_advance
+    return fn(ctx, _dp(T), _dp(p), _dp(Y), int(ld), _dp(rho), _dp(e), int(n), float(dt), _dp(substeps),
+              _stream(stream))
+
+
+def chem_advance_host(ctx, T, p, Y, rho, e, n, dt, substeps, stream=None):
+    return lib().chem_advance_host(ctx, _dp(T), _dp(p), _dp(Y), _dp(rho), _dp(e), int(n), float(dt),
+                                   _dp(substeps), _stream(stream))
+
+
+def chem_state_from_TpY(ctx, T, p, Y, ld, n, rho, e, stream=None):
+    fn = lib().chem_state_from_TpY_f64 if T.dtype.itemsize == 8 else lib().chem_state_from_TpY
+    return fn(ctx, _dp(T), _dp(p), _dp(Y), int(ld), int(n), _dp(rho), _dp(e), _stream(stream))
+
+
+def chem_temperature(ctx, Y, ld, e, n, T, stream=None):
+    return lib().chem_temperature(ctx, _dp(Y), int(ld), _dp(e), int(n), _dp(T), _stream(stream))
+
+
+def chem_rates(ctx, rho, T, Y, ld, n, dYdt, stream=None):
+    return lib().chem_rates(ctx, _dp(rho), _dp(T), _dp(Y), int(ld), int(n), _dp(dYdt), _stream(stream))
+
+
+def chem_status(ctx, stream=None):
+    s = chem_stats()
+    _check(lib().chem_status(ctx, _stream(stream), ctypes.byref(s)), "chem_status")
+    return s
+
+
+def chem_strerror(code):
+    return lib().chem_strerror(int(code)).decode()
+
+
+class Context:
+    """One mechanism on the current CUDA device; methods take torch tensors (SoA layout)."""
+
+    def __init__(self, mech, max_cells, params=None, **param_overrides):
+        self.mech = mech if isinstance(mech, Mechanism) else Mechanism(mech)
+        self.params = params if params is not None else chem_default_params(**param_overrides)
+        self.handle = chem_init(self.mech, self.params, max_cells)
+        self.ns = self.mech.ns
+
+    def close(self):
+        if self.handle is not None:
+            chem_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, **overrides):
+        for k, v in overrides.items():
+            setattr(self.params, k, v)
+        chem_set_params(self.handle, self.params)
+
+    @staticmethod
+    def _check_state(T, Y, *others):
+        n = T.shape[0]
+        for t in (T, Y) + others:
+            if t is not None and (not t.is_cuda or not t.is_contiguous()):
+                raise ValueError("tensors must be contiguous CUDA tensors")
+        return n
+
+    def advance(self, T, p, Y, rho, e, dt, substeps, stream=None):
+        n = self._check_state(T, Y, p, rho, e, substeps)
+        _check(chem_advance(self.handle, T, p, Y, Y.stride(0), rho, e, n, dt, substeps, stream), "chem_advance")
+
+    def advance_host(self, T, p, Y, rho, e, dt, substeps, stream=None):
+        _check(chem_advance_host(self.handle, T, p, Y, rho, e, T.shape[0], dt, substeps, stream),
+               "chem_advance_host")
+
+    def state_from_TpY(self, T, p, Y, rho, e, stream=None):
+        n = self._check_state(T, Y, p, rho, e)
+        _check(chem_state_from_TpY(self.handle, T, p, Y, Y.stride(0), n, rho, e, stream), "chem_state_from_TpY")
+
+    def temperature(self, Y, e, T, stream=None):
+        n = self._check_state(T, Y, e)
+        _check(chem_temperature(self.handle, Y, Y.stride(0), e, n, T, stream), "chem_temperature")
+
+    def rates(self, rho, T, Y, dYdt, stream=None):
+        n = self._check_state(T, Y, rho, dYdt)
+        _check(chem_rates(self.handle, rho, T, Y, Y.stride(0), n, dYdt, stream), "chem_rates")
+
+    def status(self, stream=None):
+        return chem_status(self.handle, stream).as_dict()

@@ -1,0 +1,478 @@
+// abi.cu -- the C ABI of libchem.so (include/chem.h): argument checks, packing of the
+// mechanism tables, workspace management and the launch sequence of one chemistry step.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/chem.h"
+#include "chem_device.cuh"
+#include "internal.h"
+
+using namespace chem;
+
+struct chem_ctx {
+  int dev = 0, sms = 0;
+  int ns = 0, nr = 0, ntb = 0;
+  unsigned char* blob = nullptr;   // device, 16-byte aligned
+  unsigned blob_bytes = 0;
+  chem_params prm{};
+  int64_t max_cells = 0;
+  Workspace* ws = nullptr;         // device
+  Workspace* ws_host = nullptr;    // pinned copy of the last call's counters
+  int* queue = nullptr;            // device [max_cells]
+  int64_t last_n = 0;
+  int bulk_grid = 0, stiff_grid = 0;
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};   // CHEM_FLAG_TIMING
+  bool timed = false;
+  // staging buffers of chem_advance_host (allocated on its first use)
+  float* hbuf = nullptr;
+  int* hsub = nullptr;
+};
+
+namespace {
+
+int cuda_fail(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return CHEM_OK;
+  std::fprintf(stderr, "libchem: %s: %s\n", what, cudaGetErrorString(e));
+  return CHEM_ECUDA;
+}
+
+unsigned align16(unsigned x) { return (x + 15u) & ~15u; }
+
+bool compiled_ns(int ns) { return ns == 9; }
+
+// Host-side packing of the mechanism into the device blob layout of chem_device.cuh.
+int pack_mechanism(const chem_mechanism* m, std::vector<unsigned char>& out, int* ntb_out) {
+  const int ns = m->ns, nr = m->nr;
+  const int nsp = (ns + 3) & ~3;
+  int ntb = 0;
+  for (int r = 0; r < nr; ++r) ntb += m->third_body[r] ? 1 : 0;
+  MechHdr h{};
+  h.ns = ns;
+  h.nr = nr;
+  h.ntb = ntb;
+  h.nsp = nsp;
+  const double T_lo = m->thermo[7], T_hi = m->thermo[8];
+  h.T_lo = static_cast<float>(T_lo);
+  h.T_hi = static_cast<float>(T_hi);
+  h.lnP0R = static_cast<float>(std::log(kP0 / kR));
+  unsigned off = align16(sizeof(MechHdr));
+  h.off_arr = off; off = align16(off + 16u * nr);
+  h.off_nuf = off; off = align16(off + 4u * nr * nsp);
+  h.off_nur = off; off = align16(off + 4u * nr * nsp);
+  h.off_dnu = off; off = align16(off + 4u * nr * nsp);
+  h.off_eff = off; off = align16(off + 4u * (ntb > 0 ? ntb : 1) * nsp);
+  h.off_rinfo = off; off = align16(off + 4u * nr);
+  h.off_W = off; off = align16(off + 4u * nsp);
+  h.off_invW = off; off = align16(off + 4u * nsp);
+  h.off_gam = off; off = align16(off + 4u * 3 * nr * 8);
+  h.off_hco = off; off = align16(off + 4u * 3 * nr * 8);
+  h.off_hsp = off; off = align16(off + 4u * 3 * ns * 8);
+  h.off_e64 = off; off = align16(off + 8u * 3 * ns * 8);
+  h.off_arr64 = off; off = align16(off + 8u * 4 * nr);
+  h.off_gam64 = off; off = align16(off + 8u * 3 * nr * 8);
+  h.off_eff64 = off; off = align16(off + 8u * (ntb > 0 ? ntb : 1) * nsp);
+  h.bytes = off;
+  out.assign(off, 0);
+  std::memcpy(out.data(), &h, sizeof(h));
+  auto F = [&](int o) { return reinterpret_cast<float*>(out.data() + o); };
+  float* arr = F(h.off_arr);
+  float *nuf = F(h.off_nuf), *nur = F(h.off_nur), *dnu = F(h.off_dnu), *eff = F(h.off_eff);
+  int* rinfo = reinterpret_cast<int*>(out.data() + h.off_rinfo);
+  float *W = F(h.off_W), *invW = F(h.off_invW), *gam = F(h.off_gam), *hco = F(h.off_hco), *hsp = F(h.off_hsp);
+  double* e64 = reinterpret_cast<double*>(out.data() + h.off_e64);
+  double* arr64 = reinterpret_cast<double*>(out.data() + h.off_arr64);
+  double* gam64 = reinterpret_cast<double*>(out.data() + h.off_gam64);
+  double* eff64 = reinterpret_cast<double*>(out.data() + h.off_eff64);
+  for (int k = 0; k < ns; ++k) {
+    W[k] = static_cast<float>(m->W[k]);
+    invW[k] = static_cast<float>(1.0 / m->W[k]);
+  }
+  // per-species coefficients per regime (0: T < T_lo, 1: in range, 2: T > T_hi), FP64
+  std::vector<double> G(3 * ns * 7), H(3 * ns * 6), E(3 * ns * 6);
+  for (int k = 0; k < ns; ++k) {
+    const double* a = m->thermo + 9 * k;
+    // in range
+    double* g = &G[(1 * ns + k) * 7];
+    g[0] = a[0]; g[1] = -a[1] / 2; g[2] = -a[2] / 6; g[3] = -a[3] / 12; g[4] = -a[4] / 20; g[5] = a[5]; g[6] = -a[6];
+    double* hh = &H[(1 * ns + k) * 6];
+    hh[0] = a[0]; hh[1] = a[1] / 2; hh[2] = a[2] / 3; hh[3] = a[3] / 4; hh[4] = a[4] / 5; hh[5] = a[5];
+    double* ee = &E[(1 * ns + k) * 6];
+    ee[0] = a[5] / m->W[k]; ee[1] = (a[0] - 1.0) / m->W[k]; ee[2] = a[1] / 2 / m->W[k];
+    ee[3] = a[2] / 3 / m->W[k]; ee[4] = a[3] / 4 / m->W[k]; ee[5] = a[4] / 5 / m->W[k];
+    // extrapolated regimes: cp frozen at the boundary value
+    for (int side = 0; side < 2; ++side) {
+      const int reg = side == 0 ? 0 : 2;
+      const double Tb = side == 0 ? T_lo : T_hi;
+      const double cpb = a[0] + Tb * (a[1] + Tb * (a[2] + Tb * (a[3] + Tb * a[4])));
+      const double hb = Tb * (a[0] + Tb * (a[1] / 2 + Tb * (a[2] / 3 + Tb * (a[3] / 4 + Tb * a[4] / 5)))) + a[5];
+      const double sb = a[0] * std::log(Tb) + Tb * (a[1] + Tb * (a[2] / 2 + Tb * (a[3] / 3 + Tb * a[4] / 4))) + a[6];
+      double* g2 = &G[(reg * ns + k) * 7];
+      g2[0] = cpb; g2[1] = g2[2] = g2[3] = g2[4] = 0.0; g2[5] = hb - cpb * Tb; g2[6] = cpb * std::log(Tb) - sb;
+      double* h2 = &H[(reg * ns + k) * 6];
+      h2[0] = cpb; h2[1] = h2[2] = h2[3] = h2[4] = 0.0; h2[5] = hb - cpb * Tb;
+      double* e2 = &E[(reg * ns + k) * 6];
+      e2[0] = (hb - cpb * Tb) / m->W[k]; e2[1] = (cpb - 1.0) / m->W[k]; e2[2] = e2[3] = e2[4] = e2[5] = 0.0;
+    }
+  }
+  for (int reg = 0; reg < 3; ++reg)
+    for (int k = 0; k < ns; ++k) {
+      for (int j = 0; j < 6; ++j) {
+        e64[(reg * ns + k) * 8 + j] = E[(reg * ns + k) * 6 + j];
+        hsp[(reg * ns + k) * 8 + j] = static_cast<float>(H[(reg * ns + k) * 6 + j]);
+      }
+      e64[(reg * ns + k) * 8 + 6] = 1.0 / m->W[k];
+    }
+  int tbrow = 0;
+  for (int r = 0; r < nr; ++r) {
+    double dn = 0.0;
+    for (int k = 0; k < ns; ++k) {
+      const int f = m->nu_f[r * ns + k], b = m->nu_r[r * ns + k];
+      nuf[r * nsp + k] = static_cast<float>(f);
+      nur[r * nsp + k] = static_cast<float>(b);
+      dnu[r * nsp + k] = static_cast<float>(b - f);
+      dn += b - f;
+    }
+    arr64[4 * r + 0] = std::log(m->A[r]);
+    arr64[4 * r + 1] = m->b[r];
+    arr64[4 * r + 2] = m->Ea[r] / kR;
+    arr64[4 * r + 3] = dn;
+    for (int j = 0; j < 4; ++j) arr[4 * r + j] = static_cast<float>(arr64[4 * r + j]);
+    int info = m->reversible[r] ? 1 : 0;
+    if (m->third_body[r]) {
+      for (int k = 0; k < ns; ++k) {
+        eff[tbrow * nsp + k] = static_cast<float>(m->eff[r * ns + k]);
+        eff64[tbrow * nsp + k] = m->eff[r * ns + k];
+      }
+      info |= (tbrow + 1) << 8;
+      ++tbrow;
+    }
+    rinfo[r] = info;
+    // reaction Gibbs / enthalpy coefficients, contracted with dnu in FP64 (no device cancellation)
+    for (int reg = 0; reg < 3; ++reg) {
+      for (int j = 0; j < 7; ++j) {
+        double sg = 0.0;
+        for (int k = 0; k < ns; ++k) sg += (m->nu_r[r * ns + k] - m->nu_f[r * ns + k]) * G[(reg * ns + k) * 7 + j];
+        gam[(reg * nr + r) * 8 + j] = static_cast<float>(sg);
+        gam64[(reg * nr + r) * 8 + j] = sg;
+      }
+      for (int j = 0; j < 6; ++j) {
+        double sh = 0.0;
+        for (int k = 0; k < ns; ++k) sh += (m->nu_r[r * ns + k] - m->nu_f[r * ns + k]) * H[(reg * ns + k) * 6 + j];
+        hco[(reg * nr + r) * 8 + j] = static_cast<float>(sh);
+      }
+    }
+  }
+  *ntb_out = ntb;
+  return CHEM_OK;
+}
+
+int check_mechanism(const chem_mechanism* m) {
+  if (!m || m->ns < 1 || m->ns > 15 || m->nr < 1 || !m->W || !m->thermo || !m->nu_f || !m->nu_r || !m->A ||
+      !m->b || !m->Ea || !m->reversible || !m->third_body)
+    return CHEM_EINVAL;
+  bool any_tb = false;
+  for (int r = 0; r < m->nr; ++r) any_tb |= m->third_body[r] != 0;
+  if (any_tb && !m->eff) return CHEM_EINVAL;
+  const double T_lo = m->thermo[7], T_hi = m->thermo[8];
+  if (!(T_lo > 0 && T_hi > T_lo)) return CHEM_EINVAL;
+  for (int k = 0; k < m->ns; ++k) {
+    if (!(m->W[k] > 0) || !std::isfinite(m->W[k])) return CHEM_EINVAL;
+    for (int j = 0; j < 7; ++j)
+      if (!std::isfinite(m->thermo[9 * k + j])) return CHEM_EINVAL;
+    if (m->thermo[9 * k + 7] != T_lo || m->thermo[9 * k + 8] != T_hi) return CHEM_EINVAL;
+  }
+  for (int r = 0; r < m->nr; ++r) {
+    if (!(m->A[r] > 0) || !std::isfinite(m->A[r]) || !std::isfinite(m->b[r]) || !std::isfinite(m->Ea[r]))
+      return CHEM_EINVAL;
+    for (int k = 0; k < m->ns; ++k) {
+      const int f = m->nu_f[r * m->ns + k], b = m->nu_r[r * m->ns + k];
+      if (f < 0 || f > 3 || b < 0 || b > 3) return CHEM_EINVAL;
+      if (m->third_body[r] && !(m->eff[r * m->ns + k] >= 0)) return CHEM_EINVAL;
+    }
+  }
+  return CHEM_OK;
+}
+
+int check_params(const chem_params* p) {
+  if (!p) return CHEM_EINVAL;
+  if (!(p->rtol > 0 && p->rtol < 1) || !(p->atol > 0 && p->atol < 1) || !std::isfinite(p->T_min) ||
+      !(p->bulk_frac > 0) || !(p->y_floor > 0) || p->k_bulk < 1 || p->k_bulk > 64 || p->k_max < 1 ||
+      (p->flags & ~(CHEM_FLAG_FP64_RATES | CHEM_FLAG_TIMING)) != 0)
+    return CHEM_EINVAL;
+  return CHEM_OK;
+}
+
+KParams kparams(const chem_params& p) {
+  KParams k;
+  k.rtol = static_cast<float>(p.rtol);
+  k.atol = static_cast<float>(p.atol);
+  k.T_min = static_cast<float>(p.T_min);
+  k.bulk_frac = static_cast<float>(p.bulk_frac);
+  k.y_floor = static_cast<float>(p.y_floor);
+  k.k_bulk = p.k_bulk;
+  k.k_max = p.k_max;
+  k.flags = p.flags;
+  return k;
+}
+
+template <typename S>
+int advance_impl(chem_ctx* ctx, S* T, S* p, S* Y, int64_t ld, const S* rho, const S* e, int64_t n, double dt,
+                 int32_t* substeps, cudaStream_t st) {
+  if (!ctx || n < 0 || !(dt > 0) || !std::isfinite(dt)) return CHEM_EINVAL;
+  if (n > ctx->max_cells) return CHEM_ENOMEM;
+  if (n > 0 && (!T || !Y || !rho || !e || !substeps || ld < n)) return CHEM_EINVAL;
+  int rc = cuda_fail(cudaSetDevice(ctx->dev), "cudaSetDevice");
+  if (rc) return rc;
+  rc = cuda_fail(cudaMemsetAsync(ctx->ws, 0, sizeof(Workspace), st), "cudaMemsetAsync");
+  if (rc) return rc;
+  ctx->last_n = n;
+  ctx->timed = false;
+  if (n > 0) {
+    AdvanceArgs<S> a;
+    a.blob = ctx->blob;
+    a.blob_bytes = ctx->blob_bytes;
+    a.prm = kparams(ctx->prm);
+    a.T = T;
+    a.p = p;
+    a.Y = Y;
+    a.ld = ld;
+    a.rho = rho;
+    a.e = e;
+    a.n = n;
+    a.dt = dt;
+    a.substeps = substeps;
+    a.ws = ctx->ws;
+    a.queue = ctx->queue;
+    long long want = (n + kBulkBlock - 1) / kBulkBlock;
+    const int bgrid = static_cast<int>(want < ctx->bulk_grid ? (want < 1 ? 1 : want) : ctx->bulk_grid);
+    int r1, r2;
+    const bool timed = (ctx->prm.flags & CHEM_FLAG_TIMING) != 0;
+    ctx->timed = timed;
+    if (timed) cudaEventRecord(ctx->ev[0], st);
+    if constexpr (sizeof(S) == 4) {
+      r1 = launch_bulk_f32(ctx->ns, a, bgrid, st);
+      if (timed && !r1) cudaEventRecord(ctx->ev[1], st);
+      r2 = r1 ? r1 : launch_stiff_f32(ctx->ns, a, ctx->stiff_grid, st);
+    } else {
+      r1 = launch_bulk_f64(ctx->ns, a, bgrid, st);
+      if (timed && !r1) cudaEventRecord(ctx->ev[1], st);
+      r2 = r1 ? r1 : launch_stiff_f64(ctx->ns, a, ctx->stiff_grid, st);
+    }
+    if (timed && !r1 && !r2) cudaEventRecord(ctx->ev[2], st);
+    if (r1 == -1 || r2 == -1) return CHEM_EUNSUPPORTED;
+    if (r1 || r2) return cuda_fail(static_cast<cudaError_t>(r1 ? r1 : r2), "kernel launch");
+  }
+  return cuda_fail(cudaMemcpyAsync(ctx->ws_host, ctx->ws, sizeof(Workspace), cudaMemcpyDeviceToHost, st),
+                   "cudaMemcpyAsync(stats)");
+}
+
+}  // namespace
+
+extern "C" {
+
+void chem_default_params(chem_params* out) {
+  if (!out) return;
+  out->rtol = 1e-5;
+  out->atol = 1e-10;
+  out->T_min = 0.0;
+  out->bulk_frac = 0.05;
+  out->y_floor = 1e-10;
+  out->k_bulk = 1;
+  out->k_max = 100000;
+  out->flags = 0;
+}
+
+int chem_init(const chem_mechanism* mech, const chem_params* params, int64_t max_cells, chem_ctx** out) {
+  if (!out) return CHEM_EINVAL;
+  *out = nullptr;
+  int rc = check_mechanism(mech);
+  if (rc) return rc;
+  chem_params prm;
+  chem_default_params(&prm);
+  if (params) {
+    if (check_params(params)) return CHEM_EINVAL;
+    prm = *params;
+  }
+  if (max_cells < 0 || max_cells > 0x7fffffffLL) return CHEM_EINVAL;
+  if (!compiled_ns(mech->ns)) return CHEM_EUNSUPPORTED;
+  chem_ctx* c = new (std::nothrow) chem_ctx();
+  if (!c) return CHEM_ENOMEM;
+  c->prm = prm;
+  c->max_cells = max_cells;
+  c->ns = mech->ns;
+  c->nr = mech->nr;
+  std::vector<unsigned char> blob;
+  pack_mechanism(mech, blob, &c->ntb);
+  c->blob_bytes = static_cast<unsigned>(blob.size());
+  auto fail = [&](int code) {
+    chem_destroy(c);
+    return code;
+  };
+  if ((rc = cuda_fail(cudaGetDevice(&c->dev), "cudaGetDevice"))) return fail(rc);
+  if ((rc = cuda_fail(cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->dev), "attr"))) return fail(rc);
+  if (cudaMalloc(&c->blob, c->blob_bytes) != cudaSuccess) return fail(CHEM_ENOMEM);
+  if ((rc = cuda_fail(cudaMemcpy(c->blob, blob.data(), c->blob_bytes, cudaMemcpyHostToDevice), "copy mechanism")))
+    return fail(rc);
+  if (cudaMalloc(&c->ws, sizeof(Workspace)) != cudaSuccess) return fail(CHEM_ENOMEM);
+  if (cudaMallocHost(&c->ws_host, sizeof(Workspace)) != cudaSuccess) return fail(CHEM_ENOMEM);
+  std::memset(c->ws_host, 0, sizeof(Workspace));
+  if (cudaMalloc(&c->queue, sizeof(int) * (max_cells > 0 ? max_cells : 1)) != cudaSuccess) return fail(CHEM_ENOMEM);
+  int bpsm = 0;
+  if (bulk_occupancy(c->ns, false, c->blob_bytes, &bpsm) != 0 || bpsm < 1) bpsm = 1;
+  c->bulk_grid = c->sms * bpsm;
+  int spsm = 0;
+  if (stiff_occupancy(c->ns, c->blob_bytes, &spsm) != 0 || spsm < 1) spsm = 1;
+  c->stiff_grid = c->sms * spsm;
+  for (auto& e : c->ev)
+    if (cudaEventCreate(&e) != cudaSuccess) return fail(CHEM_ECUDA);
+  *out = c;
+  return CHEM_OK;
+}
+
+int chem_set_params(chem_ctx* ctx, const chem_params* params) {
+  if (!ctx || check_params(params)) return CHEM_EINVAL;
+  ctx->prm = *params;
+  return CHEM_OK;
+}
+
+void chem_destroy(chem_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->dev);
+  cudaDeviceSynchronize();
+  cudaFree(ctx->blob);
+  cudaFree(ctx->ws);
+  cudaFreeHost(ctx->ws_host);
+  cudaFree(ctx->queue);
+  cudaFree(ctx->hbuf);
+  cudaFree(ctx->hsub);
+  for (auto& e : ctx->ev)
+    if (e) cudaEventDestroy(e);
+  delete ctx;
+}
+
+int chem_advance(chem_ctx* ctx, float* T, float* p, float* Y, int64_t ld, const float* rho, const float* e,
+                 int64_t n, double dt, int32_t* substeps, void* stream) {
+  return advance_impl<float>(ctx, T, p, Y, ld, rho, e, n, dt, substeps, static_cast<cudaStream_t>(stream));
+}
+
+int chem_advance_f64(chem_ctx* ctx, double* T, double* p, double* Y, int64_t ld, const double* rho,
+                     const double* e, int64_t n, double dt, int32_t* substeps, void* stream) {
+  return advance_impl<double>(ctx, T, p, Y, ld, rho, e, n, dt, substeps, static_cast<cudaStream_t>(stream));
+}
+
+int chem_advance_host(chem_ctx* ctx, float* T, float* p, float* Y, const float* rho, const float* e, int64_t n,
+                      double dt, int32_t* substeps, void* stream) {
+  if (!ctx || n < 0) return CHEM_EINVAL;
+  if (n > ctx->max_cells) return CHEM_ENOMEM;
+  if (n == 0) return CHEM_OK;
+  if (!T || !Y || !rho || !e || !substeps) return CHEM_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int rc = cuda_fail(cudaSetDevice(ctx->dev), "cudaSetDevice");
+  if (rc) return rc;
+  const int64_t cap = ctx->max_cells;
+  if (!ctx->hbuf) {
+    if (cudaMalloc(&ctx->hbuf, sizeof(float) * cap * (ctx->ns + 4)) != cudaSuccess) return CHEM_ENOMEM;
+    if (cudaMalloc(&ctx->hsub, sizeof(int) * cap) != cudaSuccess) return CHEM_ENOMEM;
+  }
+  float* dT = ctx->hbuf;
+  float* dp = dT + cap;
+  float* drho = dp + cap;
+  float* de = drho + cap;
+  float* dY = de + cap;
+  const size_t b = sizeof(float) * n;
+  if ((rc = cuda_fail(cudaMemcpyAsync(dT, T, b, cudaMemcpyHostToDevice, st), "H2D T"))) return rc;
+  if ((rc = cuda_fail(cudaMemcpyAsync(drho, rho, b, cudaMemcpyHostToDevice, st), "H2D rho"))) return rc;
+  if ((rc = cuda_fail(cudaMemcpyAsync(de, e, b, cudaMemcpyHostToDevice, st), "H2D e"))) return rc;
+  if ((rc = cuda_fail(cudaMemcpyAsync(dY, Y, b * ctx->ns, cudaMemcpyHostToDevice, st), "H2D Y"))) return rc;
+  if (p && (rc = cuda_fail(cudaMemcpyAsync(dp, p, b, cudaMemcpyHostToDevice, st), "H2D p"))) return rc;
+  rc = chem_advance(ctx, dT, p ? dp : nullptr, dY, n, drho, de, n, dt, ctx->hsub, stream);
+  if (rc) return rc;
+  if ((rc = cuda_fail(cudaMemcpyAsync(T, dT, b, cudaMemcpyDeviceToHost, st), "D2H T"))) return rc;
+  if ((rc = cuda_fail(cudaMemcpyAsync(Y, dY, b * ctx->ns, cudaMemcpyDeviceToHost, st), "D2H Y"))) return rc;
+  if (p && (rc = cuda_fail(cudaMemcpyAsync(p, dp, b, cudaMemcpyDeviceToHost, st), "D2H p"))) return rc;
+  if ((rc = cuda_fail(cudaMemcpyAsync(substeps, ctx->hsub, sizeof(int) * n, cudaMemcpyDeviceToHost, st), "D2H n")))
+    return rc;
+  return cuda_fail(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+}
+
+int chem_state_from_TpY(chem_ctx* ctx, const float* T, const float* p, const float* Y, int64_t ld, int64_t n,
+                        float* rho, float* e, void* stream) {
+  if (!ctx || n < 0 || (n > 0 && (!T || !p || !Y || !rho || !e || ld < n))) return CHEM_EINVAL;
+  if (n == 0) return CHEM_OK;
+  const int r = launch_state_from_TpY_f32(ctx->ns, ctx->blob, ctx->blob_bytes, T, p, Y, ld, n, rho, e,
+                                          &ctx->ws->status, static_cast<cudaStream_t>(stream));
+  return r == -1 ? CHEM_EUNSUPPORTED : cuda_fail(static_cast<cudaError_t>(r), "state kernel");
+}
+
+int chem_state_from_TpY_f64(chem_ctx* ctx, const double* T, const double* p, const double* Y, int64_t ld,
+                            int64_t n, double* rho, double* e, void* stream) {
+  if (!ctx || n < 0 || (n > 0 && (!T || !p || !Y || !rho || !e || ld < n))) return CHEM_EINVAL;
+  if (n == 0) return CHEM_OK;
+  const int r = launch_state_from_TpY_f64(ctx->ns, ctx->blob, ctx->blob_bytes, T, p, Y, ld, n, rho, e,
+                                          &ctx->ws->status, static_cast<cudaStream_t>(stream));
+  return r == -1 ? CHEM_EUNSUPPORTED : cuda_fail(static_cast<cudaError_t>(r), "state kernel");
+}
+
+int chem_temperature(chem_ctx* ctx, const float* Y, int64_t ld, const float* e, int64_t n, float* T, void* stream) {
+  if (!ctx || n < 0 || (n > 0 && (!Y || !e || !T || ld < n))) return CHEM_EINVAL;
+  if (n == 0) return CHEM_OK;
+  const int r = launch_temperature(ctx->ns, ctx->blob, ctx->blob_bytes, Y, ld, e, n, T, &ctx->ws->status,
+                                   static_cast<cudaStream_t>(stream));
+  return r == -1 ? CHEM_EUNSUPPORTED : cuda_fail(static_cast<cudaError_t>(r), "temperature kernel");
+}
+
+int chem_rates(chem_ctx* ctx, const float* rho, const float* T, const float* Y, int64_t ld, int64_t n, float* dYdt,
+               void* stream) {
+  if (!ctx || n < 0 || (n > 0 && (!rho || !T || !Y || !dYdt || ld < n))) return CHEM_EINVAL;
+  if (n == 0) return CHEM_OK;
+  const int r = launch_rates(ctx->ns, ctx->blob, ctx->blob_bytes, rho, T, Y, ld, n, dYdt, &ctx->ws->status,
+                             static_cast<cudaStream_t>(stream));
+  return r == -1 ? CHEM_EUNSUPPORTED : cuda_fail(static_cast<cudaError_t>(r), "rates kernel");
+}
+
+int chem_status(chem_ctx* ctx, void* stream, chem_stats* out) {
+  if (!ctx || !out) return CHEM_EINVAL;
+  int rc = cuda_fail(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)), "cudaStreamSynchronize");
+  if (rc) return rc;
+  const Workspace& w = *ctx->ws_host;
+  out->ncell = ctx->last_n;
+  out->nskipped = static_cast<int64_t>(w.nskipped);
+  out->nbulk = static_cast<int64_t>(w.nbulk);
+  out->nqueued = w.qcount;
+  out->nfailed = static_cast<int64_t>(w.nfailed);
+  out->ninvalid = static_cast<int64_t>(w.ninvalid);
+  out->substeps = static_cast<int64_t>(w.substeps);
+  out->attempts = static_cast<int64_t>(w.attempts);
+  out->newton = static_cast<int64_t>(w.newton);
+  out->bulk_ms = 0.0f;
+  out->stiff_ms = 0.0f;
+  if (ctx->timed) {
+    cudaEventElapsedTime(&out->bulk_ms, ctx->ev[0], ctx->ev[1]);
+    cudaEventElapsedTime(&out->stiff_ms, ctx->ev[1], ctx->ev[2]);
+  }
+  int status = CHEM_OK;
+  if (w.status & kFlagInvalid) status = CHEM_EINVAL;
+  if (w.status & (kFlagNoConv | kFlagTemp)) status = CHEM_ENOCONV;
+  if (w.status & kFlagMaxSteps) status = CHEM_EMAXSTEPS;
+  if (w.status & kFlagStage) status = CHEM_ECUDA;
+  out->status = status;
+  return CHEM_OK;
+}
+
+const char* chem_strerror(int code) {
+  switch (code) {
+    case CHEM_OK: return "ok";
+    case CHEM_EINVAL: return "invalid argument or input cell";
+    case CHEM_ENOMEM: return "more cells than max_cells, or device allocation failed";
+    case CHEM_EMAXSTEPS: return "a stiff cell reached k_max substeps";
+    case CHEM_ENOCONV: return "a stiff cell did not converge (step size collapsed or T(e) failed)";
+    case CHEM_ECUDA: return "CUDA runtime error";
+    case CHEM_EUNSUPPORTED: return "no kernel compiled for this mechanism shape";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

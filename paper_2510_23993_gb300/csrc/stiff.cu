@@ -1,0 +1,406 @@
+// stiff.cu -- the sparse phase of the bulk-sparse integration (Algorithm 3, section 3) with an
+// implicit integrator: every cell the bulk kernel compacted into the queue is integrated from
+// its original state over [0, dt] by an L-stable, stiffly accurate 3-stage SDIRK method of
+// order 3 (Alexander's DIRK3) with an embedded 2nd-order solution for error control.  Each
+// stage solves Y_i = y_n + h sum_{j<i} a_ij k_j + gamma h f(Y_i) by simplified Newton with the
+// dense iteration matrix I - gamma h J: J analytic in FP32, its LU factorisation with partial
+// pivoting and the triangular solves in FP64 (shared memory), the state in FP64, the
+// temperature from the internal energy by the FP64 inversion.  The error estimate is filtered
+// through (I - gamma h J)^-1 so that stiff components do not inflate it.
+//
+// The kernel is persistent (grid = SMs x resident blocks).  Each lane owns one cell at a time
+// and pulls the next one from the device queue as soon as its cell finishes (warp-aggregated
+// atomic on the queue head), so lanes of a warp stay busy on different cells while executing
+// the same substep code; this removes the warp-divergence and idle-thread costs that the paper
+// attributes to Algorithm 2, without any host round trip.
+#include "chem_device.cuh"
+#include "internal.h"
+
+namespace chem {
+
+constexpr int kNewtMax = 6;
+constexpr double kNewtTol = 0.05;   // Newton update below 5% of the error weight
+
+// Alexander's L-stable DIRK3: c = (g, (1+g)/2, 1), A = [[g,0,0],[(1-g)/2,g,0],[b1,b2,g]], b = last
+// row; g is the root of the order-3 condition sum b c^2 = 1/3 in (1/3, 1/2).  Embedded order-2
+// weights bh = (1 - bh2, bh2, 0) satisfy sum bh = 1, sum bh c = 1/2.
+constexpr double kG = 0.43586652150845895;
+constexpr double kA21 = 0.5 * (1.0 - kG);
+constexpr double kB1 = 1.2084966491760099;
+constexpr double kB2 = -0.6443631706844688;
+constexpr double kBh1 = 0.7726301276675509;
+constexpr double kBh2 = 0.2273698723324491;
+constexpr double kC2 = 0.5 * (1.0 + kG);
+
+template <int NS>
+struct Smem {
+  float* J;     // [NS*NS][B]
+  double* M;    // [NS*NS][B]
+  int t, B;
+  __device__ float& j(int r, int c) const { return J[(r * NS + c) * B + t]; }
+  __device__ double& mm(int r, int c) const { return M[(r * NS + c) * B + t]; }
+};
+
+// M = I - hh * J, then LU with partial pivoting in place (unit-lower L below the diagonal,
+// U above, reciprocal of U's diagonal on it).  Pivot rows packed 4 bits each into *piv.
+template <int NS>
+__device__ __forceinline__ bool form_and_factor(const Smem<NS>& s, double hh, uint64_t* piv) {
+#pragma unroll
+  for (int r = 0; r < NS; ++r)
+#pragma unroll
+    for (int c = 0; c < NS; ++c) s.mm(r, c) = (r == c ? 1.0 : 0.0) - hh * static_cast<double>(s.j(r, c));
+  uint64_t pv = 0;
+#pragma unroll
+  for (int k = 0; k < NS; ++k) {
+    int p = k;
+    double best = fabs(s.mm(k, k));
+#pragma unroll
+    for (int i = k + 1; i < NS; ++i) {
+      const double v = fabs(s.mm(i, k));
+      if (v > best) { best = v; p = i; }
+    }
+    if (!(best > 0.0)) return false;
+    pv |= static_cast<uint64_t>(p) << (4 * k);
+    if (p != k) {
+#pragma unroll
+      for (int c = 0; c < NS; ++c) {
+        const double t = s.mm(k, c);
+        s.mm(k, c) = s.mm(p, c);
+        s.mm(p, c) = t;
+      }
+    }
+    const double inv = 1.0 / s.mm(k, k);
+    s.mm(k, k) = inv;
+    double rowk[NS];
+#pragma unroll
+    for (int c = k + 1; c < NS; ++c) rowk[c] = s.mm(k, c);
+#pragma unroll
+    for (int i = k + 1; i < NS; ++i) {
+      const double l = s.mm(i, k) * inv;
+      s.mm(i, k) = l;
+#pragma unroll
+      for (int c = k + 1; c < NS; ++c) s.mm(i, c) = fma(-l, rowk[c], s.mm(i, c));
+    }
+  }
+  *piv = pv;
+  return true;
+}
+
+template <int NS>
+__device__ __forceinline__ void lu_solve(const Smem<NS>& s, uint64_t piv, double (&b)[NS]) {
+#pragma unroll
+  for (int k = 0; k < NS; ++k) {
+    const int p = static_cast<int>((piv >> (4 * k)) & 15u);
+#pragma unroll
+    for (int j = k + 1; j < NS; ++j) {
+      if (p == j) {
+        const double t = b[k];
+        b[k] = b[j];
+        b[j] = t;
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 1; i < NS; ++i)
+#pragma unroll
+    for (int j = 0; j < i; ++j) b[i] = fma(-s.mm(i, j), b[j], b[i]);
+#pragma unroll
+  for (int i = NS - 1; i >= 0; --i) {
+#pragma unroll
+    for (int j = i + 1; j < NS; ++j) b[i] = fma(-s.mm(i, j), b[j], b[i]);
+    b[i] *= s.mm(i, i);
+  }
+}
+
+struct CellCtx {
+  float rho, rtol, atol;
+  double e0;
+  bool fp64_rates;
+};
+
+// Solve the stage equation z = yb + hh f(z) by simplified Newton (iteration matrix factored in
+// shared memory) from the initial guess in z.  Tz: temperature guess in, temperature of the
+// last evaluated iterate out.
+template <int NS>
+__device__ __forceinline__ bool stage_newton(const MechView& m, const Smem<NS>& s, uint64_t piv, const CellCtx& c,
+                                          const double (&yb)[NS], double hh, double (&z)[NS], double& Tz,
+                                          unsigned long long& n_it) {
+  double prev = 1e300;
+  for (int it = 0; it < kNewtMax; ++it) {
+    ++n_it;
+    bool ok;
+    Tz = temperature_from_energy<NS>(m, z, c.e0, Tz, &ok);
+    if (!ok) return false;
+    float F[NS];
+    if (c.fp64_rates)
+      rates_fp64_fallback<NS>(m, c.rho, Tz, z, F);
+    else
+      rates_safe<NS>(m, c.rho, Tz, z, F);
+    double b[NS];
+#pragma unroll
+    for (int k = 0; k < NS; ++k) b[k] = -((z[k] - yb[k]) - hh * static_cast<double>(F[k]));
+    lu_solve<NS>(s, piv, b);
+    double nrm = 0.0;
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+      z[k] += b[k];
+      const double w = static_cast<double>(c.atol) + static_cast<double>(c.rtol) * fabs(z[k]);
+      nrm = fmax(nrm, fabs(b[k]) / w);
+    }
+    if (!(nrm == nrm)) return false;
+    if (nrm <= kNewtTol) return true;
+    // FP32 rates put a noise floor under the update of species in fast partial equilibrium
+    // (about 1e-6 relative): an update that has stopped contracting while already below half
+    // the error weight is at that floor and the iterate is accepted.
+    if (it > 0 && nrm <= 0.5 && nrm > 0.5 * prev) return true;
+    if (it > 0 && nrm > 2.0 * prev) return false;
+    prev = nrm;
+  }
+  return false;
+}
+
+template <int NS, typename S>
+__global__ void __launch_bounds__(kStiffBlock) stiff_kernel(const AdvanceArgs<S> a, unsigned blob_pad) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ uint64_t bar;
+  if (!stage_to_smem(smem, a.blob, a.blob_bytes, &bar, &a.ws->status)) return;
+  const MechView m = make_view(smem);
+  Smem<NS> sm;
+  sm.t = threadIdx.x;
+  sm.B = kStiffBlock;
+  sm.J = reinterpret_cast<float*>(smem + blob_pad);
+  sm.M = reinterpret_cast<double*>(smem + blob_pad + sizeof(float) * NS * NS * kStiffBlock);
+
+  const int lane = threadIdx.x & 31;
+  const int qn = min(*reinterpret_cast<volatile int*>(&a.ws->qcount), static_cast<int>(a.n));
+  const double dt = a.dt;
+  CellCtx c;
+  c.rtol = a.prm.rtol;
+  c.atol = a.prm.atol;
+  c.fp64_rates = (a.prm.flags & 1) != 0;
+
+  int cell = -1;
+  bool done = false;
+  double y[NS], t = 0.0, h = 0.0, Tc = 0.0;
+  float cvR = 1.0f;
+  int nst = 0, natt = 0;
+  unsigned long long c_sub = 0, c_fail = 0, c_att = 0, c_newt = 0;
+  int flags = 0;
+
+  while (true) {
+    // ---- refill idle lanes from the queue
+    const bool need = (cell < 0) && !done;
+    const unsigned needm = __ballot_sync(0xffffffffu, need);
+    if (needm) {
+      const int leader = __ffs(needm) - 1;
+      int base = 0;
+      if (lane == leader) base = atomicAdd(&a.ws->head, __popc(needm));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      if (need) {
+        const int q = base + __popc(needm & ((1u << lane) - 1u));
+        if (q < qn) {
+          cell = a.queue[q];
+          c.rho = static_cast<float>(a.rho[cell]);
+          c.e0 = static_cast<double>(a.e[cell]);
+#pragma unroll
+          for (int k = 0; k < NS; ++k) y[k] = static_cast<double>(a.Y[k * a.ld + cell]);
+          bool ok;
+          double cvd;
+          Tc = temperature_from_energy<NS>(m, y, c.e0, static_cast<double>(a.T[cell]), &ok, &cvd);
+          cvR = static_cast<float>(cvd);
+          t = 0.0;
+          nst = 0;
+          natt = 0;
+          // initial step: a fraction of the explicit time scale, at most dt
+          float F[NS];
+          rates_safe<NS>(m, c.rho, Tc, y, F);
+          double rate = 0.0;
+#pragma unroll
+          for (int k = 0; k < NS; ++k)
+            rate = fmax(rate, fabs(static_cast<double>(F[k])) / (fabs(y[k]) + 1e-8));
+          h = fmin(dt, fmax(1e-18, 0.05 / fmax(rate, 1e-30)));
+          if (!ok) {   // temperature not invertible: fail the cell right away
+            a.substeps[cell] = -1;
+            ++c_fail;
+            flags |= kFlagTemp;
+            cell = -1;
+          }
+        } else {
+          done = true;
+        }
+      }
+    }
+    if (__all_sync(0xffffffffu, cell < 0)) break;
+    if (cell < 0) continue;
+
+    // ---- one attempted SDIRK3 step for this lane's cell
+    ++natt;
+    ++c_att;
+    float Yf[NS];
+#pragma unroll
+    for (int k = 0; k < NS; ++k) Yf[k] = static_cast<float>(y[k]);
+    {
+      float J[NS][NS];
+      jacobian<NS>(m, c.rho, static_cast<float>(Tc), Yf, cvR, J);
+#pragma unroll
+      for (int r = 0; r < NS; ++r)
+#pragma unroll
+        for (int q = 0; q < NS; ++q) sm.j(r, q) = J[r][q];
+    }
+    uint64_t piv;
+    const double gh = kG * h;
+    double hk1[NS], hk2[NS], z[NS], base[NS];
+    double Tz = Tc;
+    bool conv = form_and_factor<NS>(sm, gh, &piv);
+    // stage 1: Y1 = y + g h f(Y1)
+#pragma unroll
+    for (int k = 0; k < NS; ++k) z[k] = y[k];
+    conv = conv && stage_newton<NS>(m, sm, piv, c, y, gh, z, Tz, c_newt);
+#pragma unroll
+    for (int k = 0; k < NS; ++k) hk1[k] = (z[k] - y[k]) * (1.0 / kG);      // h k1
+    if (conv) {   // stage 2: Y2 = y + a21 h k1 + g h f(Y2)
+#pragma unroll
+      for (int k = 0; k < NS; ++k) {
+        base[k] = y[k] + kA21 * hk1[k];
+        z[k] = y[k] + (kC2 / kG) * (z[k] - y[k]);
+      }
+      conv = stage_newton<NS>(m, sm, piv, c, base, gh, z, Tz, c_newt);
+#pragma unroll
+      for (int k = 0; k < NS; ++k) hk2[k] = (z[k] - base[k]) * (1.0 / kG);
+    }
+    if (conv) {   // stage 3: Y3 = y + b1 h k1 + b2 h k2 + g h f(Y3)
+#pragma unroll
+      for (int k = 0; k < NS; ++k) {
+        base[k] = y[k] + kB1 * hk1[k] + kB2 * hk2[k];
+        z[k] = y[k] + (z[k] - y[k]) * (1.0 / kC2);   // extrapolate Y2 to c3 = 1
+      }
+      conv = stage_newton<NS>(m, sm, piv, c, base, gh, z, Tz, c_newt);
+    }
+    bool finished = false, failed = false;
+    if (!conv) {
+      h *= 0.25;
+    } else {
+      // y_new = Y3 (stiffly accurate); error = (b - bh) . hk, filtered through (I - g h J)^-1
+      double er[NS];
+#pragma unroll
+      for (int k = 0; k < NS; ++k) {
+        const double hk3 = (z[k] - base[k]) * (1.0 / kG);
+        er[k] = (kB1 - kBh1) * hk1[k] + (kB2 - kBh2) * hk2[k] + kG * hk3;
+      }
+      lu_solve<NS>(sm, piv, er);
+      double err = 0.0;
+#pragma unroll
+      for (int k = 0; k < NS; ++k) {
+        const double w = static_cast<double>(c.atol) + static_cast<double>(c.rtol) * fmax(fabs(y[k]), fabs(z[k]));
+        err = fmax(err, fabs(er[k]) / w);
+      }
+      if (err <= 1.0) {
+        bool ok;
+        double cvd;
+        const double Tn = temperature_from_energy<NS>(m, z, c.e0, Tz, &ok, &cvd);
+        if (ok) {
+#pragma unroll
+          for (int k = 0; k < NS; ++k) y[k] = z[k];
+          Tc = Tn;
+          cvR = static_cast<float>(cvd);
+          t += h;
+          ++nst;
+          if (t >= dt * (1.0 - 1e-12)) finished = true;
+        } else {
+          err = 4.0;   // treat as a rejected step
+        }
+      }
+      double fac = 0.9 * rcbrt(fmax(err, 1e-12));   // embedded order 2: error ~ h^3
+      fac = fmin(5.0, fmax(0.2, fac));
+      h *= fac;
+    }
+    if (!finished) {
+      if (t + h > dt) h = dt - t;
+      if (h < 1e-24 * dt || h < 1e-30) { failed = true; flags |= kFlagNoConv; }
+      if (nst >= a.prm.k_max || natt >= 4 * a.prm.k_max) { failed = true; flags |= kFlagMaxSteps; }
+    }
+    if (finished) {
+      double sw = 0.0;
+#pragma unroll
+      for (int k = 0; k < NS; ++k) {
+        a.Y[k * a.ld + cell] = static_cast<S>(y[k]);
+        sw = fma(y[k], m.e64[(1 * NS + k) * 8 + 6], sw);
+      }
+      a.T[cell] = static_cast<S>(Tc);
+      if (a.p) a.p[cell] = static_cast<S>(static_cast<double>(a.rho[cell]) * kR * Tc * sw);
+      a.substeps[cell] = a.prm.k_bulk + nst;
+      c_sub += nst;
+      cell = -1;
+    } else if (failed) {
+      a.substeps[cell] = -1;
+      ++c_fail;
+      cell = -1;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    c_sub += __shfl_down_sync(0xffffffffu, c_sub, o);
+    c_fail += __shfl_down_sync(0xffffffffu, c_fail, o);
+    c_att += __shfl_down_sync(0xffffffffu, c_att, o);
+    c_newt += __shfl_down_sync(0xffffffffu, c_newt, o);
+    flags |= __shfl_down_sync(0xffffffffu, flags, o);
+  }
+  if (lane == 0) {
+    if (c_att) atomicAdd(&a.ws->attempts, c_att);
+    if (c_newt) atomicAdd(&a.ws->newton, c_newt);
+    if (c_sub) atomicAdd(&a.ws->substeps, c_sub);
+    if (c_fail) atomicAdd(&a.ws->nfailed, c_fail);
+    if (flags) atomicOr(&a.ws->status, flags);
+  }
+}
+
+// ------------------------------------------------------------------ launchers
+
+#define CHEM_FOR_EACH_NS(X) X(9)
+
+static unsigned pad128(unsigned b) { return (b + 127u) & ~127u; }
+
+size_t stiff_smem_bytes(int ns, unsigned blob_bytes) {
+  return pad128(blob_bytes) + static_cast<size_t>(ns) * ns * kStiffBlock * (sizeof(float) + sizeof(double));
+}
+
+template <int NS, typename S>
+static int stiff_launch_t(const AdvanceArgs<S>& a, int grid, cudaStream_t s) {
+  const size_t smem = stiff_smem_bytes(NS, a.blob_bytes);
+  auto k = stiff_kernel<NS, S>;
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  k<<<grid, kStiffBlock, smem, s>>>(a, pad128(a.blob_bytes));
+  return static_cast<int>(cudaGetLastError());
+}
+
+int launch_stiff_f32(int ns, const AdvanceArgs<float>& a, int grid, cudaStream_t s) {
+#define X(N) \
+  if (ns == N) return stiff_launch_t<N, float>(a, grid, s);
+  CHEM_FOR_EACH_NS(X)
+#undef X
+  return -1;
+}
+
+int launch_stiff_f64(int ns, const AdvanceArgs<double>& a, int grid, cudaStream_t s) {
+#define X(N) \
+  if (ns == N) return stiff_launch_t<N, double>(a, grid, s);
+  CHEM_FOR_EACH_NS(X)
+#undef X
+  return -1;
+}
+
+int stiff_occupancy(int ns, unsigned blob_bytes, int* blocks_per_sm) {
+#define X(N)                                                                                     \
+  if (ns == N) {                                                                                 \
+    const size_t smem = stiff_smem_bytes(N, blob_bytes);                                         \
+    cudaFuncSetAttribute(stiff_kernel<N, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
+                         static_cast<int>(smem));                                                \
+    return static_cast<int>(cudaOccupancyMaxActiveBlocksPerMultiprocessor(                      \
+        blocks_per_sm, stiff_kernel<N, float>, kStiffBlock, smem));                              \
+  }
+  CHEM_FOR_EACH_NS(X)
+#undef X
+  return -1;
+}
+
+}  // namespace chem

@@ -1,0 +1,68 @@
+"""The C-ABI library loads and exports every entry point include/chem.h declares (no GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_2510_23993_gb300 as chem
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", h)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names += re.findall(r"^\s*(?:[A-Za-z_][\w\s\*]*?)\b(chem_\w+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    chem.build()
+    return chem.lib()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for n in ("chem_init", "chem_advance", "chem_advance_f64", "chem_advance_host", "chem_destroy",
+              "chem_status", "chem_strerror", "chem_rates", "chem_temperature", "chem_state_from_TpY"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_host_logic_without_gpu(lib):
+    p = chem.chem_default_params()
+    assert p.k_bulk == 1 and p.k_max == 100000 and 0 < p.rtol < 1e-3
+    assert chem.chem_strerror(chem.CHEM_EMAXSTEPS).startswith("a stiff cell")
+    # argument checks happen on the host before any CUDA call
+    out = ctypes.c_void_p()
+    assert lib.chem_init(None, None, 10, ctypes.byref(out)) == chem.CHEM_EINVAL
+    st = chem.chem_stats()
+    assert lib.chem_status(None, None, ctypes.byref(st)) == chem.CHEM_EINVAL
+
+
+def test_bad_mechanism_rejected_before_device_use(lib, h2mech):
+    import numpy as np
+    bad = dict(h2mech)
+    bad["W"] = np.array(h2mech["W"], copy=True)
+    bad["W"][0] = -1.0
+    m = chem.Mechanism(bad)
+    out = ctypes.c_void_p()
+    assert lib.chem_init(ctypes.byref(m.c), None, 10, ctypes.byref(out)) == chem.CHEM_EINVAL
+    bad = dict(h2mech)
+    th = np.array(h2mech["thermo"], copy=True)
+    th[3, 8] = 4000.0   # species ranges must agree
+    bad["thermo"] = th
+    m = chem.Mechanism(bad)
+    assert lib.chem_init(ctypes.byref(m.c), None, 10, ctypes.byref(out)) == chem.CHEM_EINVAL
+    bad_params = chem.chem_default_params(k_bulk=0)
+    m = chem.Mechanism(h2mech)
+    assert lib.chem_init(ctypes.byref(m.c), ctypes.byref(bad_params), 10, ctypes.byref(out)) == chem.CHEM_EINVAL
