@@ -155,6 +155,26 @@ int chem_temperature(chem_ctx *ctx, const float *Y, int64_t ld, const float *e, 
 int chem_rates(chem_ctx *ctx, const float *rho, const float *T, const float *Y, int64_t ld,
                int64_t n, float *dYdt, void *stream);
 
+/* chem_advance for callers that cannot allocate device memory (no counterpart in the paper).
+ * Callers inside host callbacks or real-time loops, plugins that may only use buffers handed to
+ * them, or processes with a capped allocator cannot call chem_init, which allocates.  This entry
+ * point takes the mechanism from host memory on every call (same layout as chem_init) and keeps
+ * the packed tables (at most 64 KiB) and its scratch -- the counters and the stiff-cell queue --
+ * in fixed-size device arrays that every GPU loading the library holds until the process exits.
+ * It calls no cudaMalloc, cudaFree or other allocating routine; the caller passes the device
+ * inputs and outputs exactly as for chem_advance (ns = 9 kernels; params NULL = defaults;
+ * CHEM_FLAG_TIMING is ignored).
+ *   - at most 2,097,152 cells per call: more returns CHEM_ENOMEM with a message on stderr;
+ *   - the first call on a device looks up the device addresses of the arrays
+ *     (cudaGetSymbolAddress); make that first call before any stream capture;
+ *   - the host copy of the tables synchronizes `stream` before it starts;
+ *   - every call shares the arrays and overwrites them (the counters are cleared first): calls
+ *     that overlap on the GPU -- other streams, other threads -- race;
+ *   - stats (may be NULL) receives this call's counters; filling it synchronizes `stream`. */
+int chem_advance_noalloc(const chem_mechanism *mech, const chem_params *params, float *T, float *p,
+                         float *Y, int64_t ld, const float *rho, const float *e, int64_t n,
+                         double dt, int32_t *substeps, chem_stats *stats, void *stream);
+
 /* Synchronize `stream` and return the counters of the last advance call on this context. */
 int chem_status(chem_ctx *ctx, void *stream, chem_stats *out);
 

@@ -84,6 +84,9 @@ def lib():
         L.chem_temperature.argtypes = [vp, vp, i64, vp, i64, vp, vp]
         L.chem_rates.argtypes = [vp, vp, vp, vp, i64, i64, vp, vp]
         L.chem_status.argtypes = [vp, vp, _P(chem_stats)]
+        L.chem_advance_noalloc.argtypes = [_P(chem_mechanism), _P(chem_params), vp, vp, vp, i64, vp, vp, i64, d,
+                                           vp, _P(chem_stats), vp]
+        L.chem_advance_noalloc.restype = i32
         L.chem_strerror.argtypes = [i32]
         L.chem_strerror.restype = ctypes.c_char_p
         for name in ("chem_init", "chem_set_params", "chem_advance", "chem_advance_f64", "chem_advance_host",
@@ -173,6 +176,14 @@ def chem_advance(ctx, T, p, Y, ld, rho, e, n, dt, substeps, stream=None):
 def chem_advance_host(ctx, T, p, Y, rho, e, n, dt, substeps, stream=None):
     return lib().chem_advance_host(ctx, _dp(T), _dp(p), _dp(Y), _dp(rho), _dp(e), int(n), float(dt),
                                    _dp(substeps), _stream(stream))
+
+
+def chem_advance_noalloc(mech, params, T, p, Y, ld, rho, e, n, dt, substeps, stats=None, stream=None):
+    """chem_advance without any allocation (see include/chem.h); mech is a Mechanism."""
+    return lib().chem_advance_noalloc(ctypes.byref(mech.c), ctypes.byref(params) if params is not None else None,
+                                      _dp(T), _dp(p), _dp(Y), int(ld), _dp(rho), _dp(e), int(n), float(dt),
+                                      _dp(substeps), ctypes.byref(stats) if stats is not None else None,
+                                      _stream(stream))
 
 
 def chem_state_from_TpY(ctx, T, p, Y, ld, n, rho, e, stream=None):
