@@ -167,6 +167,7 @@ __device__ double temperature_from_energy(const MechView& m, const Y_t* Y, doubl
   mixture64<NS>(m, reg, Y, E);
   double cv = 0.0;
   bool conv = false;
+#pragma unroll 1
   for (int it = 0; it < 60; ++it) {
     const double f = fma(T, fma(T, fma(T, fma(T, fma(T, E[5], E[4]), E[3]), E[2]), E[1]), E[0]) - eR;
     cv = fma(T, fma(T, fma(T, fma(T, 5.0 * E[5], 4.0 * E[4]), 3.0 * E[3]), 2.0 * E[2]), E[1]);
@@ -279,6 +280,7 @@ __device__ __forceinline__ bool rates(const MechView& m, R rho, R T, const R* Y,
 #pragma unroll
   for (int k = 0; k < NS; ++k) w[k] = R(0);
   bool fine = true;
+#pragma unroll 1
   for (int r = 0; r < m.nr; ++r) {
     R lnkf, lnqf, lnqr;
     bool rev;
@@ -341,6 +343,7 @@ __device__ __forceinline__ void jacobian(const MechView& m, float rho, float T, 
     for (int j = 0; j < NS; ++j) J[k][j] = 0.0f;
   }
   const float T2 = T * T;
+#pragma unroll 1
   for (int r = 0; r < m.nr; ++r) {
     float lnkf, lnqf, lnqr;
     bool rev;

@@ -38,7 +38,7 @@ struct AdvanceArgs {
 };
 
 constexpr int kBulkBlock = 128;
-constexpr int kStiffBlock = 64;
+constexpr int kStiffBlock = 128;
 
 // launchers (kernels.cu / stiff.cu); return cudaError_t as int, or -1 for unsupported ns
 int launch_bulk_f32(int ns, const AdvanceArgs<float>& a, int grid, cudaStream_t s);

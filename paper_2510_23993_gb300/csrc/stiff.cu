@@ -19,7 +19,7 @@
 namespace chem {
 
 constexpr int kNewtMax = 6;
-constexpr double kNewtTol = 0.05;   // Newton update below 5% of the error weight
+constexpr double kNewtTol = 0.03;   // predicted remaining Newton error below 3% of the error weight
 
 // Alexander's L-stable DIRK3: c = (g, (1+g)/2, 1), A = [[g,0,0],[(1-g)/2,g,0],[b1,b2,g]], b = last
 // row; g is the root of the order-3 condition sum b c^2 = 1/3 in (1/3, 1/2).  Embedded order-2
@@ -32,23 +32,28 @@ constexpr double kBh1 = 0.7726301276675509;
 constexpr double kBh2 = 0.2273698723324491;
 constexpr double kC2 = 0.5 * (1.0 + kG);
 
+// Per-thread FP64 iteration matrix in shared memory, element (r, c) of thread t at
+// M[(r * NS + c) * B + t]: consecutive threads hit consecutive banks.
 template <int NS>
 struct Smem {
-  float* J;     // [NS*NS][B]
-  double* M;    // [NS*NS][B]
+  double* M;
   int t, B;
-  __device__ float& j(int r, int c) const { return J[(r * NS + c) * B + t]; }
   __device__ double& mm(int r, int c) const { return M[(r * NS + c) * B + t]; }
 };
 
-// M = I - hh * J, then LU with partial pivoting in place (unit-lower L below the diagonal,
-// U above, reciprocal of U's diagonal on it).  Pivot rows packed 4 bits each into *piv.
+// M = I - hh * J from the FP32 Jacobian in registers (FP64 in shared memory).
 template <int NS>
-__device__ __forceinline__ bool form_and_factor(const Smem<NS>& s, double hh, uint64_t* piv) {
+__device__ __forceinline__ void store_iteration_matrix(const Smem<NS>& s, const float (&J)[NS][NS], double hh) {
 #pragma unroll
   for (int r = 0; r < NS; ++r)
 #pragma unroll
-    for (int c = 0; c < NS; ++c) s.mm(r, c) = (r == c ? 1.0 : 0.0) - hh * static_cast<double>(s.j(r, c));
+    for (int c = 0; c < NS; ++c) s.mm(r, c) = (r == c ? 1.0 : 0.0) - hh * static_cast<double>(J[r][c]);
+}
+
+// LU with partial pivoting in place (unit-lower L below the diagonal, U above, reciprocal of
+// U's diagonal on it); pivot rows packed 4 bits each into *piv.
+template <int NS>
+__device__ __forceinline__ bool lu_factor(const Smem<NS>& s, uint64_t* piv) {
   uint64_t pv = 0;
 #pragma unroll
   for (int k = 0; k < NS; ++k) {
@@ -120,12 +125,16 @@ struct CellCtx {
 
 // Solve the stage equation z = yb + hh f(z) by simplified Newton (iteration matrix factored in
 // shared memory) from the initial guess in z.  Tz: temperature guess in, temperature of the
-// last evaluated iterate out.
+// last evaluated iterate out.  Convergence is judged on the weighted RMS norm of the update and
+// the contraction rate theta of the iteration: the iterate is accepted when the remaining error
+// predicted from theta, eta * |dz| with eta = theta / (1 - theta), is below kNewtTol.  eta
+// carries over between the stages of a step (first iteration of a stage uses the last value).
 template <int NS>
 __device__ __forceinline__ bool stage_newton(const MechView& m, const Smem<NS>& s, uint64_t piv, const CellCtx& c,
-                                          const double (&yb)[NS], double hh, double (&z)[NS], double& Tz,
-                                          unsigned long long& n_it) {
-  double prev = 1e300;
+                                             const double (&yb)[NS], double hh, double (&z)[NS], double& Tz,
+                                             double& eta, unsigned long long& n_it) {
+  double prev = 0.0;
+#pragma unroll 1
   for (int it = 0; it < kNewtMax; ++it) {
     ++n_it;
     bool ok;
@@ -140,20 +149,26 @@ __device__ __forceinline__ bool stage_newton(const MechView& m, const Smem<NS>& 
 #pragma unroll
     for (int k = 0; k < NS; ++k) b[k] = -((z[k] - yb[k]) - hh * static_cast<double>(F[k]));
     lu_solve<NS>(s, piv, b);
-    double nrm = 0.0;
+    float ss = 0.0f;
 #pragma unroll
     for (int k = 0; k < NS; ++k) {
       z[k] += b[k];
-      const double w = static_cast<double>(c.atol) + static_cast<double>(c.rtol) * fabs(z[k]);
-      nrm = fmax(nrm, fabs(b[k]) / w);
+      const float w = c.atol + c.rtol * fabsf(static_cast<float>(z[k]));
+      const float r = static_cast<float>(b[k]) / w;
+      ss = fmaf(r, r, ss);
     }
+    const double nrm = sqrt(static_cast<double>(ss) * (1.0 / NS));
     if (!(nrm == nrm)) return false;
-    if (nrm <= kNewtTol) return true;
-    // FP32 rates put a noise floor under the update of species in fast partial equilibrium
-    // (about 1e-6 relative): an update that has stopped contracting while already below half
-    // the error weight is at that floor and the iterate is accepted.
-    if (it > 0 && nrm <= 0.5 && nrm > 0.5 * prev) return true;
-    if (it > 0 && nrm > 2.0 * prev) return false;
+    if (it > 0) {
+      const double theta = nrm / prev;
+      if (theta >= 1.0) {
+        // not contracting: accept only at the FP32 noise floor (below half the error weight)
+        if (nrm <= 0.5 && theta < 2.0) return true;
+        return false;
+      }
+      eta = theta / (1.0 - theta);
+    }
+    if (eta * nrm <= kNewtTol || nrm <= 1e-3) return true;
     prev = nrm;
   }
   return false;
@@ -168,8 +183,7 @@ __global__ void __launch_bounds__(kStiffBlock) stiff_kernel(const AdvanceArgs<S>
   Smem<NS> sm;
   sm.t = threadIdx.x;
   sm.B = kStiffBlock;
-  sm.J = reinterpret_cast<float*>(smem + blob_pad);
-  sm.M = reinterpret_cast<double*>(smem + blob_pad + sizeof(float) * NS * NS * kStiffBlock);
+  sm.M = reinterpret_cast<double*>(smem + blob_pad);
 
   const int lane = threadIdx.x & 31;
   const int qn = min(*reinterpret_cast<volatile int*>(&a.ws->qcount), static_cast<int>(a.n));
@@ -184,6 +198,7 @@ __global__ void __launch_bounds__(kStiffBlock) stiff_kernel(const AdvanceArgs<S>
   double y[NS], t = 0.0, h = 0.0, Tc = 0.0;
   float cvR = 1.0f;
   int nst = 0, natt = 0;
+  double eta_cell = 1.0;   // Newton contraction estimate carried from step to step
   unsigned long long c_sub = 0, c_fail = 0, c_att = 0, c_newt = 0;
   int flags = 0;
 
@@ -211,15 +226,9 @@ __global__ void __launch_bounds__(kStiffBlock) stiff_kernel(const AdvanceArgs<S>
           t = 0.0;
           nst = 0;
           natt = 0;
-          // initial step: a fraction of the explicit time scale, at most dt
-          float F[NS];
-          rates_safe<NS>(m, c.rho, Tc, y, F);
-          double rate = 0.0;
-#pragma unroll
-          for (int k = 0; k < NS; ++k)
-            rate = fmax(rate, fabs(static_cast<double>(F[k])) / (fabs(y[k]) + 1e-8));
-          h = fmin(dt, fmax(1e-18, 0.05 / fmax(rate, 1e-30)));
-          if (!ok) {   // temperature not invertible: fail the cell right away
+          h = 1e-6 * dt;   // the controller grows it by up to 5x per accepted step
+          eta_cell = 1.0;
+          if (!ok) {       // temperature not invertible: fail the cell right away
             a.substeps[cell] = -1;
             ++c_fail;
             flags |= kFlagTemp;
@@ -236,49 +245,53 @@ __global__ void __launch_bounds__(kStiffBlock) stiff_kernel(const AdvanceArgs<S>
     // ---- one attempted SDIRK3 step for this lane's cell
     ++natt;
     ++c_att;
-    float Yf[NS];
-#pragma unroll
-    for (int k = 0; k < NS; ++k) Yf[k] = static_cast<float>(y[k]);
+    const double gh = kG * h;
+    uint64_t piv;
+    bool conv;
     {
+      float Yf[NS];
+#pragma unroll
+      for (int k = 0; k < NS; ++k) Yf[k] = static_cast<float>(y[k]);
       float J[NS][NS];
       jacobian<NS>(m, c.rho, static_cast<float>(Tc), Yf, cvR, J);
-#pragma unroll
-      for (int r = 0; r < NS; ++r)
-#pragma unroll
-        for (int q = 0; q < NS; ++q) sm.j(r, q) = J[r][q];
+      store_iteration_matrix<NS>(sm, J, gh);
     }
-    uint64_t piv;
-    const double gh = kG * h;
+    conv = lu_factor<NS>(sm, &piv);
+    // stage s solves Y_s = y + sum_j A_sj hk_j + g h f(Y_s), hk_j = h k_j, starting from
+    // y + sum_j P_sj hk_j (extrapolation of the previous stages to c_s)
     double hk1[NS], hk2[NS], z[NS], base[NS];
     double Tz = Tc;
-    bool conv = form_and_factor<NS>(sm, gh, &piv);
-    // stage 1: Y1 = y + g h f(Y1)
+    double eta = eta_cell;
 #pragma unroll
-    for (int k = 0; k < NS; ++k) z[k] = y[k];
-    conv = conv && stage_newton<NS>(m, sm, piv, c, y, gh, z, Tz, c_newt);
-#pragma unroll
-    for (int k = 0; k < NS; ++k) hk1[k] = (z[k] - y[k]) * (1.0 / kG);      // h k1
-    if (conv) {   // stage 2: Y2 = y + a21 h k1 + g h f(Y2)
+    for (int k = 0; k < NS; ++k) {
+      hk1[k] = 0.0;
+      hk2[k] = 0.0;
+    }
+#pragma unroll 1
+    for (int st = 0; st < 3 && conv; ++st) {
+      const double a1 = st == 1 ? kA21 : (st == 2 ? kB1 : 0.0);
+      const double a2 = st == 2 ? kB2 : 0.0;
+      const double p1 = st == 1 ? kC2 : (st == 2 ? kA21 / kC2 : 0.0);
+      const double p2 = st == 2 ? kG / kC2 : 0.0;
 #pragma unroll
       for (int k = 0; k < NS; ++k) {
-        base[k] = y[k] + kA21 * hk1[k];
-        z[k] = y[k] + (kC2 / kG) * (z[k] - y[k]);
+        base[k] = y[k] + a1 * hk1[k] + a2 * hk2[k];
+        z[k] = y[k] + p1 * hk1[k] + p2 * hk2[k];
       }
-      conv = stage_newton<NS>(m, sm, piv, c, base, gh, z, Tz, c_newt);
+      conv = stage_newton<NS>(m, sm, piv, c, base, gh, z, Tz, eta, c_newt);
+      if (st < 2) {
 #pragma unroll
-      for (int k = 0; k < NS; ++k) hk2[k] = (z[k] - base[k]) * (1.0 / kG);
-    }
-    if (conv) {   // stage 3: Y3 = y + b1 h k1 + b2 h k2 + g h f(Y3)
-#pragma unroll
-      for (int k = 0; k < NS; ++k) {
-        base[k] = y[k] + kB1 * hk1[k] + kB2 * hk2[k];
-        z[k] = y[k] + (z[k] - y[k]) * (1.0 / kC2);   // extrapolate Y2 to c3 = 1
+        for (int k = 0; k < NS; ++k) {
+          const double hk = (z[k] - base[k]) * (1.0 / kG);
+          if (st == 0) hk1[k] = hk; else hk2[k] = hk;
+        }
       }
-      conv = stage_newton<NS>(m, sm, piv, c, base, gh, z, Tz, c_newt);
     }
+    eta_cell = fmax(eta, 0.05);
     bool finished = false, failed = false;
     if (!conv) {
       h *= 0.25;
+      eta_cell = 1.0;
     } else {
       // y_new = Y3 (stiffly accurate); error = (b - bh) . hk, filtered through (I - g h J)^-1
       double er[NS];
@@ -361,7 +374,7 @@ __global__ void __launch_bounds__(kStiffBlock) stiff_kernel(const AdvanceArgs<S>
 static unsigned pad128(unsigned b) { return (b + 127u) & ~127u; }
 
 size_t stiff_smem_bytes(int ns, unsigned blob_bytes) {
-  return pad128(blob_bytes) + static_cast<size_t>(ns) * ns * kStiffBlock * (sizeof(float) + sizeof(double));
+  return pad128(blob_bytes) + static_cast<size_t>(ns) * ns * kStiffBlock * sizeof(double);
 }
 
 template <int NS, typename S>
