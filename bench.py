@@ -117,7 +117,8 @@ def run_gpu(args, rank, world, local_rank, dist):
     dev = torch.device("cuda", local_rank)
     mech, T, p, Y, hot = _field(seed=rank)
     n = T.size
-    ctx = chem.Context(mech, max_cells=n, rtol=args.rtol, atol=args.atol, flags=chem.CHEM_FLAG_TIMING)
+    ctx = chem.Context(mech, max_cells=n, rtol=args.rtol, atol=args.atol,
+                       flags=chem.CHEM_FLAG_TIMING | chem.CHEM_FLAG_ORDER_RATE)
     tT, tp, tY = (torch.from_numpy(a).to(dev) for a in (T, p, Y))
     rho, e = torch.empty_like(tT), torch.empty_like(tT)
     ctx.state_from_TpY(tT, tp, tY, rho, e)

@@ -80,6 +80,13 @@ typedef struct {
 /* chem_params.flags: record CUDA events around the bulk and the stiff kernel of each advance call
  * (on the call's stream); chem_status then reports their durations.  Not for graph capture. */
 #define CHEM_FLAG_TIMING 2
+/* chem_params.flags: hand the stiff cells to the persistent stiff kernel most expensive first
+ * (counting sort by a cost bucket between the two kernels), which shortens the tail of that
+ * kernel.  ORDER_RATE keys on dt * sum_k |dY_k/dt| at the bulk step; ORDER_PREV keys on the
+ * substep count that the previous call left in substeps[i] (the array is then read on entry:
+ * pass the previous call's output, e.g. in a time-stepping loop). */
+#define CHEM_FLAG_ORDER_RATE 4
+#define CHEM_FLAG_ORDER_PREV 8
 
 /* Counters of the last advance call (see chem_status). */
 typedef struct {
@@ -98,7 +105,7 @@ typedef struct {
 } chem_stats;
 
 /* Defaults: rtol 1e-5, atol 1e-10, T_min 0, bulk_frac 0.05, y_floor 1e-10, k_bulk 1,
- * k_max 100000, flags 0. */
+ * k_max 100000, flags CHEM_FLAG_ORDER_RATE. */
 void chem_default_params(chem_params *out);
 
 /* Create a context for one mechanism on the current CUDA device.  Copies the mechanism into

@@ -22,6 +22,8 @@ CHEM_ECUDA = -5
 CHEM_EUNSUPPORTED = -6
 CHEM_FLAG_FP64_RATES = 1
 CHEM_FLAG_TIMING = 2
+CHEM_FLAG_ORDER_RATE = 4
+CHEM_FLAG_ORDER_PREV = 8
 
 _P = ctypes.POINTER
 _c_void_p = ctypes.c_void_p

@@ -22,6 +22,8 @@ struct chem_ctx {
   Workspace* ws = nullptr;         // device
   Workspace* ws_host = nullptr;    // pinned copy of the last call's counters
   int* queue = nullptr;            // device [max_cells]
+  int* queue2 = nullptr;           // device [max_cells], the queue in cost order
+  unsigned char* qkey = nullptr;   // device [max_cells], cost bucket of each queue entry
   int64_t last_n = 0;
   int bulk_grid = 0, stiff_grid = 0;
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};   // CHEM_FLAG_TIMING
@@ -200,7 +202,7 @@ int check_params(const chem_params* p) {
   if (!p) return CHEM_EINVAL;
   if (!(p->rtol > 0 && p->rtol < 1) || !(p->atol > 0 && p->atol < 1) || !std::isfinite(p->T_min) ||
       !(p->bulk_frac > 0) || !(p->y_floor > 0) || p->k_bulk < 1 || p->k_bulk > 64 || p->k_max < 1 ||
-      (p->flags & ~(CHEM_FLAG_FP64_RATES | CHEM_FLAG_TIMING)) != 0)
+      (p->flags & ~(CHEM_FLAG_FP64_RATES | CHEM_FLAG_TIMING | CHEM_FLAG_ORDER_RATE | CHEM_FLAG_ORDER_PREV)) != 0)
     return CHEM_EINVAL;
   return CHEM_OK;
 }
@@ -246,20 +248,26 @@ int advance_impl(chem_ctx* ctx, S* T, S* p, S* Y, int64_t ld, const S* rho, cons
     a.substeps = substeps;
     a.ws = ctx->ws;
     a.queue = ctx->queue;
+    const bool order = (ctx->prm.flags & (CHEM_FLAG_ORDER_RATE | CHEM_FLAG_ORDER_PREV)) != 0;
+    a.qkey = order ? ctx->qkey : nullptr;
     long long want = (n + kBulkBlock - 1) / kBulkBlock;
     const int bgrid = static_cast<int>(want < ctx->bulk_grid ? (want < 1 ? 1 : want) : ctx->bulk_grid);
     int r1, r2;
     const bool timed = (ctx->prm.flags & CHEM_FLAG_TIMING) != 0;
     ctx->timed = timed;
     if (timed) cudaEventRecord(ctx->ev[0], st);
+    AdvanceArgs<S> b = a;   // the stiff kernel reads the cost-ordered queue when ordering is on
+    if (order) b.queue = ctx->queue2;
     if constexpr (sizeof(S) == 4) {
       r1 = launch_bulk_f32(ctx->ns, a, bgrid, st);
+      if (!r1 && order) r1 = launch_order_queue(ctx->ws, ctx->queue, ctx->qkey, ctx->queue2, n, st);
       if (timed && !r1) cudaEventRecord(ctx->ev[1], st);
-      r2 = r1 ? r1 : launch_stiff_f32(ctx->ns, a, ctx->stiff_grid, st);
+      r2 = r1 ? r1 : launch_stiff_f32(ctx->ns, b, ctx->stiff_grid, st);
     } else {
       r1 = launch_bulk_f64(ctx->ns, a, bgrid, st);
+      if (!r1 && order) r1 = launch_order_queue(ctx->ws, ctx->queue, ctx->qkey, ctx->queue2, n, st);
       if (timed && !r1) cudaEventRecord(ctx->ev[1], st);
-      r2 = r1 ? r1 : launch_stiff_f64(ctx->ns, a, ctx->stiff_grid, st);
+      r2 = r1 ? r1 : launch_stiff_f64(ctx->ns, b, ctx->stiff_grid, st);
     }
     if (timed && !r1 && !r2) cudaEventRecord(ctx->ev[2], st);
     if (r1 == -1 || r2 == -1) return CHEM_EUNSUPPORTED;
@@ -282,7 +290,7 @@ void chem_default_params(chem_params* out) {
   out->y_floor = 1e-10;
   out->k_bulk = 1;
   out->k_max = 100000;
-  out->flags = 0;
+  out->flags = CHEM_FLAG_ORDER_RATE;
 }
 
 int chem_init(const chem_mechanism* mech, const chem_params* params, int64_t max_cells, chem_ctx** out) {
@@ -319,7 +327,10 @@ int chem_init(const chem_mechanism* mech, const chem_params* params, int64_t max
   if (cudaMalloc(&c->ws, sizeof(Workspace)) != cudaSuccess) return fail(CHEM_ENOMEM);
   if (cudaMallocHost(&c->ws_host, sizeof(Workspace)) != cudaSuccess) return fail(CHEM_ENOMEM);
   std::memset(c->ws_host, 0, sizeof(Workspace));
-  if (cudaMalloc(&c->queue, sizeof(int) * (max_cells > 0 ? max_cells : 1)) != cudaSuccess) return fail(CHEM_ENOMEM);
+  const int64_t qcap = max_cells > 0 ? max_cells : 1;
+  if (cudaMalloc(&c->queue, sizeof(int) * qcap) != cudaSuccess) return fail(CHEM_ENOMEM);
+  if (cudaMalloc(&c->queue2, sizeof(int) * qcap) != cudaSuccess) return fail(CHEM_ENOMEM);
+  if (cudaMalloc(&c->qkey, qcap) != cudaSuccess) return fail(CHEM_ENOMEM);
   int bpsm = 0;
   if (bulk_occupancy(c->ns, false, c->blob_bytes, &bpsm) != 0 || bpsm < 1) bpsm = 1;
   c->bulk_grid = c->sms * bpsm;
@@ -346,6 +357,8 @@ void chem_destroy(chem_ctx* ctx) {
   cudaFree(ctx->ws);
   cudaFreeHost(ctx->ws_host);
   cudaFree(ctx->queue);
+  cudaFree(ctx->queue2);
+  cudaFree(ctx->qkey);
   cudaFree(ctx->hbuf);
   cudaFree(ctx->hsub);
   for (auto& e : ctx->ev)

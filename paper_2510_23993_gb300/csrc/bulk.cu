@@ -31,6 +31,7 @@ __global__ void __launch_bounds__(kBulkBlock) bulk_kernel(const AdvanceArgs<S> a
        base += stride) {
     const long long i = base + lane;
     bool enqueue = false;
+    int bucket = 0;
     if (i < a.n) {
       const S rho = a.rho[i], e = a.e[i], T = a.T[i];
       S y[NS];
@@ -48,6 +49,7 @@ __global__ void __launch_bounds__(kBulkBlock) bulk_kernel(const AdvanceArgs<S> a
         ++c_skip;
       } else {
         bool pass;
+        float cost = 0.0f;   // dt * sum_k |dY_k/dt| at the first bulk substep (queue ordering key)
         double Tn = temperature_from_energy<NS>(m, y, static_cast<double>(e), static_cast<double>(T), &pass);
         const float rhof = static_cast<float>(rho);
         for (int s = 0; s < kb && pass; ++s) {
@@ -55,6 +57,11 @@ __global__ void __launch_bounds__(kBulkBlock) bulk_kernel(const AdvanceArgs<S> a
 #pragma unroll
           for (int k = 0; k < NS; ++k) yf[k] = static_cast<float>(y[k]);
           pass = rates<NS, float>(m, rhof, static_cast<float>(Tn), yf, f0);
+          if (s == 0) {
+#pragma unroll
+            for (int k = 0; k < NS; ++k) cost += fabsf(f0[k]);
+            cost *= static_cast<float>(dt);
+          }
           S y1[NS];
           float chg = 0.0f;
 #pragma unroll
@@ -96,6 +103,16 @@ __global__ void __launch_bounds__(kBulkBlock) bulk_kernel(const AdvanceArgs<S> a
           ++c_bulk;
         } else {
           enqueue = true;
+          if (a.qkey) {
+            float lk;
+            if (a.prm.flags & kFlagOrderPrev) {   // substep count of the previous call on this cell
+              const int prev = a.substeps[i];
+              lk = 4.0f * __log2f(static_cast<float>(prev > 0 ? (prev < (1 << 24) ? prev : (1 << 24)) : 1));
+            } else {                               // explicit rate magnitude over dt
+              lk = 2.0f * __log2f(fmaxf(cost, 1e-30f)) + 32.0f;
+            }
+            bucket = static_cast<int>(fminf(fmaxf(lk, 0.0f), static_cast<float>(kNumBuckets - 1)));
+          }
         }
       }
     }
@@ -106,7 +123,11 @@ __global__ void __launch_bounds__(kBulkBlock) bulk_kernel(const AdvanceArgs<S> a
       int off = 0;
       if (lane == leader) off = atomicAdd(&a.ws->qcount, __popc(mask));
       off = __shfl_sync(0xffffffffu, off, leader);
-      if (enqueue) a.queue[off + __popc(mask & ((1u << lane) - 1u))] = static_cast<int>(i);
+      if (enqueue) {
+        const int slot = off + __popc(mask & ((1u << lane) - 1u));
+        a.queue[slot] = static_cast<int>(i);
+        if (a.qkey) a.qkey[slot] = static_cast<unsigned char>(bucket);
+      }
     }
   }
   // counters: warp reduction, one atomic per warp
@@ -124,6 +145,38 @@ __global__ void __launch_bounds__(kBulkBlock) bulk_kernel(const AdvanceArgs<S> a
       atomicOr(&a.ws->status, kFlagInvalid);
     }
   }
+}
+
+// Counting sort of the stiff queue by cost bucket, most expensive bucket first (one block): a
+// longest-first order shortens the tail of the persistent stiff kernel, whose duration is set
+// by the cells that start last.
+__global__ void __launch_bounds__(1024) order_queue_kernel(Workspace* ws, const int* queue, const unsigned char* qkey,
+                                                           int* queue_out, long long n) {
+  __shared__ int hist[kNumBuckets];
+  __shared__ int off[kNumBuckets];
+  const int qn = static_cast<int>(min(static_cast<long long>(*reinterpret_cast<volatile int*>(&ws->qcount)), n));
+  for (int b = threadIdx.x; b < kNumBuckets; b += blockDim.x) hist[b] = 0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < qn; i += blockDim.x) atomicAdd(&hist[qkey[i] & (kNumBuckets - 1)], 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int b = kNumBuckets - 1; b >= 0; --b) {
+      off[b] = acc;
+      acc += hist[b];
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < qn; i += blockDim.x) {
+    const int pos = atomicAdd(&off[qkey[i] & (kNumBuckets - 1)], 1);
+    queue_out[pos] = queue[i];
+  }
+}
+
+int launch_order_queue(Workspace* ws, const int* queue, const unsigned char* qkey, int* queue_out, long long n,
+                       cudaStream_t s) {
+  order_queue_kernel<<<1, 1024, 0, s>>>(ws, queue, qkey, queue_out, n);
+  return static_cast<int>(cudaGetLastError());
 }
 
 // rho = p / (R T sum Y/W), e = R * e/R(T) (FP64)

@@ -159,7 +159,7 @@ __device__ __forceinline__ void mixture64(const MechView& m, int reg, const Y_t*
 template <int NS, typename Y_t>
 __device__ double temperature_from_energy(const MechView& m, const Y_t* Y, double e0, double T,
                                           bool* ok, double* cv_out = nullptr) {
-  const double eR = e0 / kR;
+  const double eR = e0 * (1.0 / kR);
   double lo = kTbrLo, hi = kTbrHi;
   if (!(T > lo && T < hi)) T = 1000.0;
   int reg = regime_of(static_cast<float>(T), m.T_lo, m.T_hi);
@@ -184,7 +184,9 @@ __device__ double temperature_from_energy(const MechView& m, const Y_t* Y, doubl
       mixture64<NS>(m, reg, Y, E);
       continue;
     }
-    if (fabs(dT) <= 1e-10 * T) { conv = true; break; }
+    // the step used c_v to ~1e-7 relative, so the error left after it is ~1e-7 |dT| + O(dT^2):
+    // below 1e-14 T once |dT| <= 3e-8 T
+    if (fabs(dT) <= 3e-8 * T) { conv = true; break; }
   }
   if (cv_out) *cv_out = cv;
   *ok = conv && (T > kTbrLo) && (T < kTbrHi);

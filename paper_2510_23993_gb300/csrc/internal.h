@@ -35,7 +35,13 @@ struct AdvanceArgs {
   int* substeps;
   Workspace* ws;
   int* queue;                    // [max_cells]
+  unsigned char* qkey;           // [max_cells] cost bucket of each queue entry, or null (no ordering)
 };
+
+// cost keys of the stiff queue (chem_params.flags bits, see include/chem.h)
+constexpr int kFlagOrderRate = 4;   // bucket of log2(dt * sum_k |dY_k/dt|) at the bulk step
+constexpr int kFlagOrderPrev = 8;   // bucket of log2 of the cell's substep count of the previous call
+constexpr int kNumBuckets = 64;
 
 constexpr int kBulkBlock = 128;
 constexpr int kStiffBlock = 128;
@@ -46,6 +52,9 @@ int launch_bulk_f64(int ns, const AdvanceArgs<double>& a, int grid, cudaStream_t
 int launch_stiff_f32(int ns, const AdvanceArgs<float>& a, int grid, cudaStream_t s);
 int launch_stiff_f64(int ns, const AdvanceArgs<double>& a, int grid, cudaStream_t s);
 size_t stiff_smem_bytes(int ns, unsigned blob_bytes);
+// counting sort of the queue by cost bucket, most expensive first: queue -> queue_out
+int launch_order_queue(Workspace* ws, const int* queue, const unsigned char* qkey, int* queue_out,
+                       long long n, cudaStream_t s);
 size_t bulk_smem_bytes(unsigned blob_bytes);
 int stiff_occupancy(int ns, unsigned blob_bytes, int* blocks_per_sm);
 int bulk_occupancy(int ns, bool f64, unsigned blob_bytes, int* blocks_per_sm);
