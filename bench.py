@@ -191,7 +191,7 @@ def run_gpu(args, rank, world, local_rank, dist):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-            "config": _config(n, args), "roofline": roof, "e2e": e2e, "gpu_launches": 2 * args.steps * world,
+            "config": _config(n, args), "roofline": roof, "e2e": e2e, "gpu_launches": 3 * args.steps * world,   # bulk + queue order + stiff
             "clocks": clk,
             "stiff": {"queued_cells": stats[-1]["nqueued"], "bulk_cells": stats[-1]["nbulk"],
                       "substeps_per_stiff_cell": stats[-1]["substeps"] / max(1, stats[-1]["nqueued"]),

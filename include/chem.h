@@ -145,6 +145,38 @@ int chem_advance_f64(chem_ctx *ctx, double *T, double *p, double *Y, int64_t ld,
 int chem_advance_host(chem_ctx *ctx, float *T, float *p, float *Y, const float *rho,
                       const float *e, int64_t n, double dt, int32_t *substeps, void *stream);
 
+/* One box of a block-structured AMR hierarchy (Sec. 2.3): its own SoA arrays (device memory,
+ * caller-owned; the same meaning and layout as the arguments of chem_advance) and its chemistry
+ * step dt (under temporal subcycling a level-l box advances dt0 / r^l).  level is informational. */
+typedef struct {
+  float *T, *p, *Y;          /* p may be NULL */
+  int64_t ld;                /* leading dimension of Y (>= n) */
+  const float *rho, *e;
+  int32_t *substeps;
+  int64_t n;                 /* cells in the box */
+  double dt;                 /* s */
+  int32_t level;
+} chem_box;
+
+/* Register the box table used by chem_advance_boxes (a set-up call: it synchronizes the device
+ * and allocates the device copy of the table; the boxes' arrays are referenced, not copied).
+ * At most 4096 boxes and max_cells cells in total (else CHEM_EINVAL / CHEM_ENOMEM).  A
+ * previously captured graph is released. */
+int chem_boxes_set(chem_ctx *ctx, const chem_box *boxes, int32_t nbox);
+
+/* Advance every cell of every registered box over its box's dt in one bulk launch and one
+ * persistent stiff launch over all boxes (the multigrid kernel fusion of Sec. 3.2 / App. E: cells
+ * find their box through a prefix sum of box sizes, no data is copied).  Same per-cell semantics
+ * and status reporting as chem_advance.  Asynchronous, no host synchronization. */
+int chem_advance_boxes(chem_ctx *ctx, void *stream);
+
+/* Capture chem_advance_boxes on `stream` (a non-default stream) into a CUDA graph kept by the
+ * context; chem_boxes_launch then replays the whole chemistry step as one graph launch.  The
+ * graph refers to the registered box arrays: refill them in place between launches.  Not with
+ * CHEM_FLAG_TIMING. */
+int chem_boxes_capture(chem_ctx *ctx, void *stream);
+int chem_boxes_launch(chem_ctx *ctx, void *stream);
+
 /* Density and internal energy from (T, p, Y) (ideal gas; e = sum_k Y_k u_k(T)), computed in
  * FP64 and rounded to the output type.  Device pointers; asynchronous. */
 int chem_state_from_TpY(chem_ctx *ctx, const float *T, const float *p, const float *Y,

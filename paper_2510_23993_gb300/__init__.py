@@ -44,6 +44,12 @@ class chem_params(ctypes.Structure):
                 ("k_bulk", ctypes.c_int32), ("k_max", ctypes.c_int32), ("flags", ctypes.c_int32)]
 
 
+class chem_box(ctypes.Structure):
+    _fields_ = [("T", ctypes.c_void_p), ("p", ctypes.c_void_p), ("Y", ctypes.c_void_p), ("ld", ctypes.c_int64),
+                ("rho", ctypes.c_void_p), ("e", ctypes.c_void_p), ("substeps", ctypes.c_void_p),
+                ("n", ctypes.c_int64), ("dt", ctypes.c_double), ("level", ctypes.c_int32)]
+
+
 class chem_stats(ctypes.Structure):
     _fields_ = [("ncell", ctypes.c_int64), ("nskipped", ctypes.c_int64), ("nbulk", ctypes.c_int64),
                 ("nqueued", ctypes.c_int64), ("nfailed", ctypes.c_int64), ("ninvalid", ctypes.c_int64),
@@ -89,6 +95,12 @@ def lib():
         L.chem_advance_noalloc.argtypes = [_P(chem_mechanism), _P(chem_params), vp, vp, vp, i64, vp, vp, i64, d,
                                            vp, _P(chem_stats), vp]
         L.chem_advance_noalloc.restype = i32
+        L.chem_boxes_set.argtypes = [vp, _P(chem_box), i32]
+        L.chem_advance_boxes.argtypes = [vp, vp]
+        L.chem_boxes_capture.argtypes = [vp, vp]
+        L.chem_boxes_launch.argtypes = [vp, vp]
+        for name in ("chem_boxes_set", "chem_advance_boxes", "chem_boxes_capture", "chem_boxes_launch"):
+            getattr(L, name).restype = i32
         L.chem_strerror.argtypes = [i32]
         L.chem_strerror.restype = ctypes.c_char_p
         for name in ("chem_init", "chem_set_params", "chem_advance", "chem_advance_f64", "chem_advance_host",
@@ -188,6 +200,28 @@ def chem_advance_noalloc(mech, params, T, p, Y, ld, rho, e, n, dt, substeps, sta
                                       _stream(stream))
 
 
+def chem_boxes_set(ctx, boxes):
+    """boxes: sequence of dicts with tensors T, p, Y, rho, e, substeps and floats dt, level."""
+    arr = (chem_box * len(boxes))()
+    for k, b in enumerate(boxes):
+        arr[k] = chem_box(b["T"].data_ptr(), b["p"].data_ptr() if b.get("p") is not None else None,
+                          b["Y"].data_ptr(), b["Y"].stride(0), b["rho"].data_ptr(), b["e"].data_ptr(),
+                          b["substeps"].data_ptr(), b["T"].shape[0], float(b["dt"]), int(b.get("level", 0)))
+    return lib().chem_boxes_set(ctx, arr, len(boxes))
+
+
+def chem_advance_boxes(ctx, stream=None):
+    return lib().chem_advance_boxes(ctx, _stream(stream))
+
+
+def chem_boxes_capture(ctx, stream):
+    return lib().chem_boxes_capture(ctx, _stream(stream))
+
+
+def chem_boxes_launch(ctx, stream=None):
+    return lib().chem_boxes_launch(ctx, _stream(stream))
+
+
 def chem_state_from_TpY(ctx, T, p, Y, ld, n, rho, e, stream=None):
     fn = lib().chem_state_from_TpY_f64 if T.dtype.itemsize == 8 else lib().chem_state_from_TpY
     return fn(ctx, _dp(T), _dp(p), _dp(Y), int(ld), int(n), _dp(rho), _dp(e), _stream(stream))
@@ -266,3 +300,16 @@ class Context:
 
     def status(self, stream=None):
         return chem_status(self.handle, stream).as_dict()
+
+    def set_boxes(self, boxes):
+        self._boxes = list(boxes)   # the library references these tensors
+        _check(chem_boxes_set(self.handle, self._boxes), "chem_boxes_set")
+
+    def advance_boxes(self, stream=None):
+        _check(chem_advance_boxes(self.handle, stream), "chem_advance_boxes")
+
+    def capture_boxes(self, stream):
+        _check(chem_boxes_capture(self.handle, stream), "chem_boxes_capture")
+
+    def launch_boxes(self, stream=None):
+        _check(chem_boxes_launch(self.handle, stream), "chem_boxes_launch")

@@ -27,6 +27,13 @@ struct chem_ctx {
   int64_t last_n = 0;
   int bulk_grid = 0, stiff_grid = 0;
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};   // CHEM_FLAG_TIMING
+  // box table (chem_boxes_set)
+  DevBox<float>* boxes = nullptr;
+  int* box_off = nullptr;
+  int nbox = 0;
+  int64_t box_cells = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
   bool timed = false;
   // staging buffers of chem_advance_host (allocated on its first use)
   float* hbuf = nullptr;
@@ -248,6 +255,9 @@ int advance_impl(chem_ctx* ctx, S* T, S* p, S* Y, int64_t ld, const S* rho, cons
     a.substeps = substeps;
     a.ws = ctx->ws;
     a.queue = ctx->queue;
+    a.boxes = nullptr;
+    a.box_off = nullptr;
+    a.nbox = 0;
     const bool order = (ctx->prm.flags & (CHEM_FLAG_ORDER_RATE | CHEM_FLAG_ORDER_PREV)) != 0;
     a.qkey = order ? ctx->qkey : nullptr;
     long long want = (n + kBulkBlock - 1) / kBulkBlock;
@@ -363,6 +373,10 @@ void chem_destroy(chem_ctx* ctx) {
   cudaFree(ctx->hsub);
   for (auto& e : ctx->ev)
     if (e) cudaEventDestroy(e);
+  if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+  if (ctx->graph) cudaGraphDestroy(ctx->graph);
+  cudaFree(ctx->boxes);
+  cudaFree(ctx->box_off);
   delete ctx;
 }
 
@@ -409,6 +423,120 @@ int chem_advance_host(chem_ctx* ctx, float* T, float* p, float* Y, const float* 
   if ((rc = cuda_fail(cudaMemcpyAsync(substeps, ctx->hsub, sizeof(int) * n, cudaMemcpyDeviceToHost, st), "D2H n")))
     return rc;
   return cuda_fail(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+}
+
+int chem_boxes_set(chem_ctx* ctx, const chem_box* boxes, int32_t nbox) {
+  if (!ctx || nbox < 1 || nbox > kMaxBoxes || !boxes) return CHEM_EINVAL;
+  std::vector<DevBox<float>> tab(nbox);
+  std::vector<int> off(nbox + 1);
+  int64_t total = 0;
+  for (int b = 0; b < nbox; ++b) {
+    const chem_box& x = boxes[b];
+    if (x.n < 0 || (x.n > 0 && (!x.T || !x.Y || !x.rho || !x.e || !x.substeps || x.ld < x.n)) || !(x.dt > 0) ||
+        !std::isfinite(x.dt))
+      return CHEM_EINVAL;
+    tab[b].T = x.T;
+    tab[b].p = x.p;
+    tab[b].Y = x.Y;
+    tab[b].rho = x.rho;
+    tab[b].e = x.e;
+    tab[b].substeps = x.substeps;
+    tab[b].ld = x.ld;
+    tab[b].n = x.n;
+    tab[b].off = total;
+    tab[b].dt = x.dt;
+    tab[b].level = x.level;
+    tab[b].pad = 0;
+    off[b] = static_cast<int>(total);
+    total += x.n;
+    if (total > ctx->max_cells) return CHEM_ENOMEM;
+  }
+  off[nbox] = static_cast<int>(total);
+  int rc = cuda_fail(cudaSetDevice(ctx->dev), "cudaSetDevice");
+  if (rc) return rc;
+  cudaDeviceSynchronize();   // the previous table may be in use by queued work
+  if (ctx->graph_exec) { cudaGraphExecDestroy(ctx->graph_exec); ctx->graph_exec = nullptr; }
+  if (ctx->graph) { cudaGraphDestroy(ctx->graph); ctx->graph = nullptr; }
+  cudaFree(ctx->boxes);
+  cudaFree(ctx->box_off);
+  ctx->boxes = nullptr;
+  ctx->box_off = nullptr;
+  ctx->nbox = 0;
+  if (cudaMalloc(&ctx->boxes, sizeof(DevBox<float>) * nbox) != cudaSuccess) return CHEM_ENOMEM;
+  if (cudaMalloc(&ctx->box_off, sizeof(int) * (nbox + 1)) != cudaSuccess) return CHEM_ENOMEM;
+  if ((rc = cuda_fail(cudaMemcpy(ctx->boxes, tab.data(), sizeof(DevBox<float>) * nbox, cudaMemcpyHostToDevice),
+                      "copy box table")))
+    return rc;
+  if ((rc = cuda_fail(cudaMemcpy(ctx->box_off, off.data(), sizeof(int) * (nbox + 1), cudaMemcpyHostToDevice),
+                      "copy box offsets")))
+    return rc;
+  ctx->nbox = nbox;
+  ctx->box_cells = total;
+  return CHEM_OK;
+}
+
+int chem_advance_boxes(chem_ctx* ctx, void* stream) {
+  if (!ctx || ctx->nbox < 1) return CHEM_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int rc = cuda_fail(cudaSetDevice(ctx->dev), "cudaSetDevice");
+  if (rc) return rc;
+  if ((rc = cuda_fail(cudaMemsetAsync(ctx->ws, 0, sizeof(Workspace), st), "cudaMemsetAsync"))) return rc;
+  ctx->last_n = ctx->box_cells;
+  ctx->timed = false;
+  const int64_t n = ctx->box_cells;
+  if (n > 0) {
+    AdvanceArgs<float> a{};
+    a.blob = ctx->blob;
+    a.blob_bytes = ctx->blob_bytes;
+    a.prm = kparams(ctx->prm);
+    a.n = n;
+    a.ws = ctx->ws;
+    a.queue = ctx->queue;
+    a.boxes = ctx->boxes;
+    a.box_off = ctx->box_off;
+    a.nbox = ctx->nbox;
+    const bool order = (ctx->prm.flags & (CHEM_FLAG_ORDER_RATE | CHEM_FLAG_ORDER_PREV)) != 0;
+    a.qkey = order ? ctx->qkey : nullptr;
+    AdvanceArgs<float> b = a;
+    if (order) b.queue = ctx->queue2;
+    long long want = (n + kBulkBlock - 1) / kBulkBlock;
+    const int bgrid = static_cast<int>(want < ctx->bulk_grid ? (want < 1 ? 1 : want) : ctx->bulk_grid);
+    int r1 = launch_bulk_f32(ctx->ns, a, bgrid, st);
+    if (!r1 && order) r1 = launch_order_queue(ctx->ws, ctx->queue, ctx->qkey, ctx->queue2, n, st);
+    int r2 = r1 ? r1 : launch_stiff_f32(ctx->ns, b, ctx->stiff_grid, st);
+    if (r1 == -1 || r2 == -1) return CHEM_EUNSUPPORTED;
+    if (r1 || r2) return cuda_fail(static_cast<cudaError_t>(r1 ? r1 : r2), "kernel launch");
+  }
+  return cuda_fail(cudaMemcpyAsync(ctx->ws_host, ctx->ws, sizeof(Workspace), cudaMemcpyDeviceToHost, st),
+                   "cudaMemcpyAsync(stats)");
+}
+
+int chem_boxes_capture(chem_ctx* ctx, void* stream) {
+  if (!ctx || ctx->nbox < 1 || (ctx->prm.flags & CHEM_FLAG_TIMING)) return CHEM_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (!st) return CHEM_EINVAL;   // capture needs a non-default stream
+  int rc = cuda_fail(cudaSetDevice(ctx->dev), "cudaSetDevice");
+  if (rc) return rc;
+  if (ctx->graph_exec) { cudaGraphExecDestroy(ctx->graph_exec); ctx->graph_exec = nullptr; }
+  if (ctx->graph) { cudaGraphDestroy(ctx->graph); ctx->graph = nullptr; }
+  if ((rc = cuda_fail(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "begin capture"))) return rc;
+  const int adv = chem_advance_boxes(ctx, stream);
+  cudaGraph_t g = nullptr;
+  const cudaError_t ec = cudaStreamEndCapture(st, &g);
+  if (adv) {
+    if (g) cudaGraphDestroy(g);
+    return adv;
+  }
+  if ((rc = cuda_fail(ec, "end capture"))) return rc;
+  ctx->graph = g;
+  return cuda_fail(cudaGraphInstantiate(&ctx->graph_exec, g, 0), "graph instantiate");
+}
+
+int chem_boxes_launch(chem_ctx* ctx, void* stream) {
+  if (!ctx || !ctx->graph_exec) return CHEM_EINVAL;
+  ctx->last_n = ctx->box_cells;
+  ctx->timed = false;
+  return cuda_fail(cudaGraphLaunch(ctx->graph_exec, static_cast<cudaStream_t>(stream)), "graph launch");
 }
 
 int chem_state_from_TpY(chem_ctx* ctx, const float* T, const float* p, const float* Y, int64_t ld, int64_t n,

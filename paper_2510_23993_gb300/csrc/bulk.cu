@@ -21,31 +21,35 @@ __global__ void __launch_bounds__(kBulkBlock) bulk_kernel(const AdvanceArgs<S> a
   __shared__ uint64_t bar;
   if (!stage_to_smem(smem, a.blob, a.blob_bytes, &bar, &a.ws->status)) return;
   const MechView m = make_view(smem);
+  int* soff = reinterpret_cast<int*>(smem + ((a.blob_bytes + 127u) & ~127u));
+  if (a.nbox > 0) stage_box_offsets(soff, a.box_off, a.nbox);
   const int lane = threadIdx.x & 31;
   const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
   unsigned long long c_skip = 0, c_bulk = 0, c_inv = 0;
-  const double dt = a.dt;
   const int kb = a.prm.k_bulk;
-  const float h = static_cast<float>(dt / kb);
   for (long long base = static_cast<long long>(blockIdx.x) * blockDim.x + (threadIdx.x & ~31); base < a.n;
        base += stride) {
-    const long long i = base + lane;
+    const long long g = base + lane;
     bool enqueue = false;
     int bucket = 0;
-    if (i < a.n) {
-      const S rho = a.rho[i], e = a.e[i], T = a.T[i];
+    if (g < a.n) {
+      const CellRef<S> cr = locate(a, soff, g);
+      const long long i = cr.i;
+      const double dt = cr.dt;
+      const float h = static_cast<float>(dt / kb);
+      const S rho = cr.rho[i], e = cr.e[i], T = cr.T[i];
       S y[NS];
       bool valid = finite_(rho) && rho > S(0) && finite_(e) && finite_(T) && T > S(0);
 #pragma unroll
       for (int k = 0; k < NS; ++k) {
-        y[k] = a.Y[k * a.ld + i];
+        y[k] = cr.Y[k * cr.ld + i];
         valid = valid && finite_(y[k]) && y[k] > S(-1e-6);
       }
       if (!valid) {
-        a.substeps[i] = -1;
+        cr.sub[i] = -1;
         ++c_inv;
       } else if (T < static_cast<S>(a.prm.T_min)) {
-        a.substeps[i] = 0;
+        cr.sub[i] = 0;
         ++c_skip;
       } else {
         bool pass;
@@ -94,19 +98,19 @@ __global__ void __launch_bounds__(kBulkBlock) bulk_kernel(const AdvanceArgs<S> a
           double sw = 0.0;
 #pragma unroll
           for (int k = 0; k < NS; ++k) {
-            a.Y[k * a.ld + i] = y[k];
+            cr.Y[k * cr.ld + i] = y[k];
             sw = fma(static_cast<double>(y[k]), static_cast<double>(m.invW[k]), sw);
           }
-          a.T[i] = static_cast<S>(Tn);
-          if (a.p) a.p[i] = static_cast<S>(static_cast<double>(rho) * kR * Tn * sw);
-          a.substeps[i] = kb;
+          cr.T[i] = static_cast<S>(Tn);
+          if (cr.p) cr.p[i] = static_cast<S>(static_cast<double>(rho) * kR * Tn * sw);
+          cr.sub[i] = kb;
           ++c_bulk;
         } else {
           enqueue = true;
           if (a.qkey) {
             float lk;
             if (a.prm.flags & kFlagOrderPrev) {   // substep count of the previous call on this cell
-              const int prev = a.substeps[i];
+              const int prev = cr.sub[i];
               lk = 4.0f * __log2f(static_cast<float>(prev > 0 ? (prev < (1 << 24) ? prev : (1 << 24)) : 1));
             } else {                               // explicit rate magnitude over dt
               lk = 2.0f * __log2f(fmaxf(cost, 1e-30f)) + 32.0f;
@@ -125,7 +129,7 @@ __global__ void __launch_bounds__(kBulkBlock) bulk_kernel(const AdvanceArgs<S> a
       off = __shfl_sync(0xffffffffu, off, leader);
       if (enqueue) {
         const int slot = off + __popc(mask & ((1u << lane) - 1u));
-        a.queue[slot] = static_cast<int>(i);
+        a.queue[slot] = static_cast<int>(g);
         if (a.qkey) a.qkey[slot] = static_cast<unsigned char>(bucket);
       }
     }
@@ -249,7 +253,9 @@ __global__ void __launch_bounds__(kBulkBlock) rates_kernel(const unsigned char* 
 
 #define CHEM_FOR_EACH_NS(X) X(9)
 
-size_t bulk_smem_bytes(unsigned blob_bytes) { return blob_bytes; }
+size_t bulk_smem_bytes(unsigned blob_bytes, int nbox) {
+  return ((blob_bytes + 127u) & ~127u) + box_smem_bytes(nbox);
+}
 
 static int grid_for(long long n) {
   int dev = 0, sms = 1;
@@ -264,8 +270,9 @@ static int grid_for(long long n) {
 template <int NS, typename S>
 static int bulk_launch_t(const AdvanceArgs<S>& a, int grid, cudaStream_t s) {
   auto k = bulk_kernel<NS, S>;
-  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(a.blob_bytes));
-  k<<<grid, kBulkBlock, a.blob_bytes, s>>>(a);
+  const size_t smem = bulk_smem_bytes(a.blob_bytes, a.nbox);
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  k<<<grid, kBulkBlock, smem, s>>>(a);
   return static_cast<int>(cudaGetLastError());
 }
 

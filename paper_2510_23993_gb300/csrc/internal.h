@@ -19,6 +19,20 @@ struct KParams {
   int k_bulk, k_max, flags;
 };
 
+// One AMR box of a box-table advance: the box's own SoA arrays and its chemistry step.
+template <typename S>
+struct DevBox {
+  S* T;
+  S* p;
+  S* Y;
+  const S* rho;
+  const S* e;
+  int* substeps;
+  long long ld, n, off;          // leading dimension, cells, first global cell index
+  double dt;                     // chemistry step of the box (dt0 / r^level under subcycling)
+  int level, pad;
+};
+
 template <typename S>
 struct AdvanceArgs {
   const unsigned char* blob;     // packed mechanism (global, 16-byte aligned)
@@ -36,7 +50,67 @@ struct AdvanceArgs {
   Workspace* ws;
   int* queue;                    // [max_cells]
   unsigned char* qkey;           // [max_cells] cost bucket of each queue entry, or null (no ordering)
+  const DevBox<S>* boxes;        // box table (nbox > 0): global cell g lives in the box whose
+  const int* box_off;            //   [off_b, off_b + n_b) range; box_off[b] = off_b, b <= nbox
+  int nbox;                      // 0: flat arrays T, p, Y, rho, e, substeps of n cells, step dt
 };
+
+constexpr int kMaxBoxes = 4096;
+
+// Where cell g lives: flat arrays, or the box found by binary search over the box offsets
+// (staged in shared memory as soff[0..nbox]).
+template <typename S>
+struct CellRef {
+  S* T;
+  S* p;
+  S* Y;
+  const S* rho;
+  const S* e;
+  int* sub;
+  long long ld, i;
+  double dt;
+};
+
+template <typename S>
+__device__ __forceinline__ CellRef<S> locate(const AdvanceArgs<S>& a, const int* soff, long long g) {
+  CellRef<S> r;
+  if (a.nbox == 0) {
+    r.T = a.T;
+    r.p = a.p;
+    r.Y = a.Y;
+    r.rho = a.rho;
+    r.e = a.e;
+    r.sub = a.substeps;
+    r.ld = a.ld;
+    r.i = g;
+    r.dt = a.dt;
+    return r;
+  }
+  int lo = 0, hi = a.nbox - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (static_cast<long long>(soff[mid]) <= g) lo = mid; else hi = mid - 1;
+  }
+  const DevBox<S>& b = a.boxes[lo];
+  r.T = b.T;
+  r.p = b.p;
+  r.Y = b.Y;
+  r.rho = b.rho;
+  r.e = b.e;
+  r.sub = b.substeps;
+  r.ld = b.ld;
+  r.i = g - soff[lo];
+  r.dt = b.dt;
+  return r;
+}
+
+// Copy the box offsets into shared memory (all threads of the block call it).
+__device__ __forceinline__ void stage_box_offsets(int* soff, const int* off, int nbox) {
+  for (int b = threadIdx.x; b <= nbox; b += blockDim.x) soff[b] = off[b];
+  __syncthreads();
+}
+
+__host__ __device__ inline unsigned box_smem_bytes(int nbox) { return nbox > 0 ? ((4u * (nbox + 1) + 127u) & ~127u) : 0u; }
 
 // cost keys of the stiff queue (chem_params.flags bits, see include/chem.h)
 constexpr int kFlagOrderRate = 4;   // bucket of log2(dt * sum_k |dY_k/dt|) at the bulk step
@@ -51,11 +125,11 @@ int launch_bulk_f32(int ns, const AdvanceArgs<float>& a, int grid, cudaStream_t 
 int launch_bulk_f64(int ns, const AdvanceArgs<double>& a, int grid, cudaStream_t s);
 int launch_stiff_f32(int ns, const AdvanceArgs<float>& a, int grid, cudaStream_t s);
 int launch_stiff_f64(int ns, const AdvanceArgs<double>& a, int grid, cudaStream_t s);
-size_t stiff_smem_bytes(int ns, unsigned blob_bytes);
+size_t stiff_smem_bytes(int ns, unsigned blob_bytes, int nbox);
 // counting sort of the queue by cost bucket, most expensive first: queue -> queue_out
 int launch_order_queue(Workspace* ws, const int* queue, const unsigned char* qkey, int* queue_out,
                        long long n, cudaStream_t s);
-size_t bulk_smem_bytes(unsigned blob_bytes);
+size_t bulk_smem_bytes(unsigned blob_bytes, int nbox);
 int stiff_occupancy(int ns, unsigned blob_bytes, int* blocks_per_sm);
 int bulk_occupancy(int ns, bool f64, unsigned blob_bytes, int* blocks_per_sm);
 

@@ -259,6 +259,9 @@ extern "C" int chem_advance_noalloc(const chem_mechanism* mech, const chem_param
     a.ws = ws;
     a.queue = queue;
     a.qkey = nullptr;   // no cost ordering here: the stiff kernel takes cells in compaction order
+    a.boxes = nullptr;
+    a.box_off = nullptr;
+    a.nbox = 0;
     int bpsm = 1, spsm = 1;
     if (bulk_occupancy(mech->ns, false, bytes, &bpsm) != 0 || bpsm < 1) bpsm = 1;
     if (stiff_occupancy(mech->ns, bytes, &spsm) != 0 || spsm < 1) spsm = 1;

@@ -180,14 +180,15 @@ __global__ void __launch_bounds__(kStiffBlock) stiff_kernel(const AdvanceArgs<S>
   __shared__ uint64_t bar;
   if (!stage_to_smem(smem, a.blob, a.blob_bytes, &bar, &a.ws->status)) return;
   const MechView m = make_view(smem);
+  int* soff = reinterpret_cast<int*>(smem + blob_pad);
+  if (a.nbox > 0) stage_box_offsets(soff, a.box_off, a.nbox);
   Smem<NS> sm;
   sm.t = threadIdx.x;
   sm.B = kStiffBlock;
-  sm.M = reinterpret_cast<double*>(smem + blob_pad);
+  sm.M = reinterpret_cast<double*>(smem + blob_pad + box_smem_bytes(a.nbox));
 
   const int lane = threadIdx.x & 31;
   const int qn = min(*reinterpret_cast<volatile int*>(&a.ws->qcount), static_cast<int>(a.n));
-  const double dt = a.dt;
   CellCtx c;
   c.rtol = a.prm.rtol;
   c.atol = a.prm.atol;
@@ -195,6 +196,7 @@ __global__ void __launch_bounds__(kStiffBlock) stiff_kernel(const AdvanceArgs<S>
 
   int cell = -1;
   bool done = false;
+  double dt = 0.0;
   double y[NS], t = 0.0, h = 0.0, Tc = 0.0;
   float cvR = 1.0f;
   int nst = 0, natt = 0;
@@ -215,13 +217,16 @@ __global__ void __launch_bounds__(kStiffBlock) stiff_kernel(const AdvanceArgs<S>
         const int q = base + __popc(needm & ((1u << lane) - 1u));
         if (q < qn) {
           cell = a.queue[q];
-          c.rho = static_cast<float>(a.rho[cell]);
-          c.e0 = static_cast<double>(a.e[cell]);
+          const CellRef<S> cr = locate(a, soff, cell);
+          const long long i = cr.i;
+          dt = cr.dt;
+          c.rho = static_cast<float>(cr.rho[i]);
+          c.e0 = static_cast<double>(cr.e[i]);
 #pragma unroll
-          for (int k = 0; k < NS; ++k) y[k] = static_cast<double>(a.Y[k * a.ld + cell]);
+          for (int k = 0; k < NS; ++k) y[k] = static_cast<double>(cr.Y[k * cr.ld + i]);
           bool ok;
           double cvd;
-          Tc = temperature_from_energy<NS>(m, y, c.e0, static_cast<double>(a.T[cell]), &ok, &cvd);
+          Tc = temperature_from_energy<NS>(m, y, c.e0, static_cast<double>(cr.T[i]), &ok, &cvd);
           cvR = static_cast<float>(cvd);
           t = 0.0;
           nst = 0;
@@ -229,7 +234,7 @@ __global__ void __launch_bounds__(kStiffBlock) stiff_kernel(const AdvanceArgs<S>
           h = 1e-6 * dt;   // the controller grows it by up to 5x per accepted step
           eta_cell = 1.0;
           if (!ok) {       // temperature not invertible: fail the cell right away
-            a.substeps[cell] = -1;
+            cr.sub[i] = -1;
             ++c_fail;
             flags |= kFlagTemp;
             cell = -1;
@@ -333,19 +338,22 @@ __global__ void __launch_bounds__(kStiffBlock) stiff_kernel(const AdvanceArgs<S>
       if (nst >= a.prm.k_max || natt >= 4 * a.prm.k_max) { failed = true; flags |= kFlagMaxSteps; }
     }
     if (finished) {
+      const CellRef<S> cr = locate(a, soff, cell);   // recomputed: keeps the loop's registers free
+      const long long i = cr.i;
       double sw = 0.0;
 #pragma unroll
       for (int k = 0; k < NS; ++k) {
-        a.Y[k * a.ld + cell] = static_cast<S>(y[k]);
+        cr.Y[k * cr.ld + i] = static_cast<S>(y[k]);
         sw = fma(y[k], m.e64[(1 * NS + k) * 8 + 6], sw);
       }
-      a.T[cell] = static_cast<S>(Tc);
-      if (a.p) a.p[cell] = static_cast<S>(static_cast<double>(a.rho[cell]) * kR * Tc * sw);
-      a.substeps[cell] = a.prm.k_bulk + nst;
+      cr.T[i] = static_cast<S>(Tc);
+      if (cr.p) cr.p[i] = static_cast<S>(static_cast<double>(cr.rho[i]) * kR * Tc * sw);
+      cr.sub[i] = a.prm.k_bulk + nst;
       c_sub += nst;
       cell = -1;
     } else if (failed) {
-      a.substeps[cell] = -1;
+      const CellRef<S> cr = locate(a, soff, cell);
+      cr.sub[cr.i] = -1;
       ++c_fail;
       cell = -1;
     }
@@ -373,13 +381,13 @@ __global__ void __launch_bounds__(kStiffBlock) stiff_kernel(const AdvanceArgs<S>
 
 static unsigned pad128(unsigned b) { return (b + 127u) & ~127u; }
 
-size_t stiff_smem_bytes(int ns, unsigned blob_bytes) {
-  return pad128(blob_bytes) + static_cast<size_t>(ns) * ns * kStiffBlock * sizeof(double);
+size_t stiff_smem_bytes(int ns, unsigned blob_bytes, int nbox) {
+  return pad128(blob_bytes) + box_smem_bytes(nbox) + static_cast<size_t>(ns) * ns * kStiffBlock * sizeof(double);
 }
 
 template <int NS, typename S>
 static int stiff_launch_t(const AdvanceArgs<S>& a, int grid, cudaStream_t s) {
-  const size_t smem = stiff_smem_bytes(NS, a.blob_bytes);
+  const size_t smem = stiff_smem_bytes(NS, a.blob_bytes, a.nbox);
   auto k = stiff_kernel<NS, S>;
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   k<<<grid, kStiffBlock, smem, s>>>(a, pad128(a.blob_bytes));
@@ -405,7 +413,7 @@ int launch_stiff_f64(int ns, const AdvanceArgs<double>& a, int grid, cudaStream_
 int stiff_occupancy(int ns, unsigned blob_bytes, int* blocks_per_sm) {
 #define X(N)                                                                                     \
   if (ns == N) {                                                                                 \
-    const size_t smem = stiff_smem_bytes(N, blob_bytes);                                         \
+    const size_t smem = stiff_smem_bytes(N, blob_bytes, 0);                                      \
     cudaFuncSetAttribute(stiff_kernel<N, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
                          static_cast<int>(smem));                                                \
     return static_cast<int>(cudaOccupancyMaxActiveBlocksPerMultiprocessor(                      \
