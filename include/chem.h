@@ -214,6 +214,30 @@ int chem_advance_noalloc(const chem_mechanism *mech, const chem_params *params, 
                          float *Y, int64_t ld, const float *rho, const float *e, int64_t n,
                          double dt, int32_t *substeps, chem_stats *stats, void *stream);
 
+/* Result of chem_tune. */
+typedef struct {
+  int32_t k_bulk;                /* chosen explicit bulk substeps per cell */
+  int32_t flags;                 /* chosen queue-order flag (0 or CHEM_FLAG_ORDER_RATE) */
+  int32_t bulk_blocks_per_sm;    /* resident blocks per SM of the bulk kernel grid */
+  int32_t stiff_blocks_per_sm;   /* resident blocks per SM of the persistent stiff kernel */
+  float best_ms, default_ms;     /* timed advance with the chosen / the incoming settings */
+  int32_t trials;                /* timed advances run */
+  int32_t from_cache;            /* 1 if the choice came from the cache file */
+} chem_tune_result;
+
+/* Autotuner of the launch configuration (the paper tuned K_max and the bulk-to-sparse threshold
+ * by hand, Sec. 3.2 / App. D): times chem_advance on the caller's field (device arrays as for
+ * chem_advance) for candidate values of k_bulk (1..3), the stiff-queue order and the resident
+ * blocks per SM of both kernels (coordinate descent, best of two repetitions), applies the
+ * fastest to the context and returns it.  T, p, Y are restored to their input values on return
+ * (the advanced state is discarded).  A set-up call: it allocates temporary device copies of T,
+ * p, Y and synchronizes `stream`.  cache_path (may be NULL) names a text file: a matching entry
+ * (mechanism shape, log2 of the cell count, dt, GPU name) is applied without trials, and a tuned
+ * choice is appended. */
+int chem_tune(chem_ctx *ctx, float *T, float *p, float *Y, int64_t ld, const float *rho,
+              const float *e, int64_t n, double dt, int32_t *substeps, const char *cache_path,
+              chem_tune_result *out, void *stream);
+
 /* Synchronize `stream` and return the counters of the last advance call on this context. */
 int chem_status(chem_ctx *ctx, void *stream, chem_stats *out);
 

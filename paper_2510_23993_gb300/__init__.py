@@ -50,6 +50,15 @@ class chem_box(ctypes.Structure):
                 ("n", ctypes.c_int64), ("dt", ctypes.c_double), ("level", ctypes.c_int32)]
 
 
+class chem_tune_result(ctypes.Structure):
+    _fields_ = [("k_bulk", ctypes.c_int32), ("flags", ctypes.c_int32), ("bulk_blocks_per_sm", ctypes.c_int32),
+                ("stiff_blocks_per_sm", ctypes.c_int32), ("best_ms", ctypes.c_float), ("default_ms", ctypes.c_float),
+                ("trials", ctypes.c_int32), ("from_cache", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class chem_stats(ctypes.Structure):
     _fields_ = [("ncell", ctypes.c_int64), ("nskipped", ctypes.c_int64), ("nbulk", ctypes.c_int64),
                 ("nqueued", ctypes.c_int64), ("nfailed", ctypes.c_int64), ("ninvalid", ctypes.c_int64),
@@ -101,6 +110,8 @@ def lib():
         L.chem_boxes_launch.argtypes = [vp, vp]
         for name in ("chem_boxes_set", "chem_advance_boxes", "chem_boxes_capture", "chem_boxes_launch"):
             getattr(L, name).restype = i32
+        L.chem_tune.argtypes = [vp, vp, vp, vp, i64, vp, vp, i64, d, vp, ctypes.c_char_p, _P(chem_tune_result), vp]
+        L.chem_tune.restype = i32
         L.chem_strerror.argtypes = [i32]
         L.chem_strerror.restype = ctypes.c_char_p
         for name in ("chem_init", "chem_set_params", "chem_advance", "chem_advance_f64", "chem_advance_host",
@@ -300,6 +311,14 @@ class Context:
 
     def status(self, stream=None):
         return chem_status(self.handle, stream).as_dict()
+
+    def tune(self, T, p, Y, rho, e, dt, substeps, cache_path=None, stream=None):
+        """Autotune the launch configuration on this field (inputs are left unchanged)."""
+        res = chem_tune_result()
+        cp = cache_path.encode() if cache_path else None
+        _check(lib().chem_tune(self.handle, _dp(T), _dp(p), _dp(Y), Y.stride(0), _dp(rho), _dp(e), T.shape[0],
+                               float(dt), _dp(substeps), cp, ctypes.byref(res), _stream(stream)), "chem_tune")
+        return res.as_dict()
 
     def set_boxes(self, boxes):
         self._boxes = list(boxes)   # the library references these tensors

@@ -289,6 +289,32 @@ int advance_impl(chem_ctx* ctx, S* T, S* p, S* Y, int64_t ld, const S* rho, cons
 
 }  // namespace
 
+namespace chem {
+// launch settings of a context, used by the tuner (tune.cu)
+void ctx_get_launch(const chem_ctx* c, int* bulk_grid, int* stiff_grid, int* sms, int* ns, int* nr) {
+  *bulk_grid = c->bulk_grid;
+  *stiff_grid = c->stiff_grid;
+  *sms = c->sms;
+  *ns = c->ns;
+  *nr = c->nr;
+}
+void ctx_set_launch(chem_ctx* c, int bulk_grid, int stiff_grid) {
+  c->bulk_grid = bulk_grid > 0 ? bulk_grid : 1;
+  c->stiff_grid = stiff_grid > 0 ? stiff_grid : 1;
+}
+void ctx_get_params(const chem_ctx* c, chem_params* p) { *p = c->prm; }
+int occupancy_bulk(const chem_ctx* c) {
+  int b = 0;
+  if (bulk_occupancy(c->ns, false, c->blob_bytes, &b) != 0 || b < 1) b = 1;
+  return b;
+}
+int occupancy_stiff(const chem_ctx* c) {
+  int b = 0;
+  if (stiff_occupancy(c->ns, c->blob_bytes, &b) != 0 || b < 1) b = 1;
+  return b;
+}
+}  // namespace chem
+
 extern "C" {
 
 void chem_default_params(chem_params* out) {
