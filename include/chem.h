@@ -238,6 +238,17 @@ int chem_tune(chem_ctx *ctx, float *T, float *p, float *Y, int64_t ld, const flo
               const float *e, int64_t n, double dt, int32_t *substeps, const char *cache_path,
               chem_tune_result *out, void *stream);
 
+/* The BF16 tensor-core GEMM (tcgen05, FP32 accumulation) that the surrogate's kernels are built
+ * on, exposed for verification:
+ *   C[m*ldc + n] = epi( sum_k A[m*sam + k*sak] * B[n*sbn + k*sbk] ),  m < M, n < N (<= 256), k < K
+ * A and B are FP32 device arrays, rounded to BF16 on load.  epi: 0 store, 1 + bias[n], 2 + bias[n]
+ * with gelu(z) also stored in C2 (same layout), 3 atomic add into C (required when ksplit > 1,
+ * K split over ksplit CTAs).  *status (device int) gets bit 32 if an MMA completion wait timed out.
+ * Asynchronous on `stream`. */
+int chem_tc_gemm(const float *A, int64_t sam, int64_t sak, const float *B, int64_t sbn, int64_t sbk,
+                 float *C, int64_t ldc, const float *bias, float *C2, int32_t M, int32_t N, int32_t K,
+                 int32_t epi, int32_t ksplit, int32_t *status, void *stream);
+
 /* Synchronize `stream` and return the counters of the last advance call on this context. */
 int chem_status(chem_ctx *ctx, void *stream, chem_stats *out);
 

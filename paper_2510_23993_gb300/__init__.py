@@ -112,6 +112,8 @@ def lib():
             getattr(L, name).restype = i32
         L.chem_tune.argtypes = [vp, vp, vp, vp, i64, vp, vp, i64, d, vp, ctypes.c_char_p, _P(chem_tune_result), vp]
         L.chem_tune.restype = i32
+        L.chem_tc_gemm.argtypes = [vp, i64, i64, vp, i64, i64, vp, i64, vp, vp, i32, i32, i32, i32, i32, vp, vp]
+        L.chem_tc_gemm.restype = i32
         L.chem_strerror.argtypes = [i32]
         L.chem_strerror.restype = ctypes.c_char_p
         for name in ("chem_init", "chem_set_params", "chem_advance", "chem_advance_f64", "chem_advance_host",
@@ -209,6 +211,11 @@ def chem_advance_noalloc(mech, params, T, p, Y, ld, rho, e, n, dt, substeps, sta
                                       _dp(T), _dp(p), _dp(Y), int(ld), _dp(rho), _dp(e), int(n), float(dt),
                                       _dp(substeps), ctypes.byref(stats) if stats is not None else None,
                                       _stream(stream))
+
+
+def chem_tc_gemm(A, sam, sak, B, sbn, sbk, C, ldc, bias, C2, M, N, K, epi, ksplit, status, stream=None):
+    return lib().chem_tc_gemm(_dp(A), int(sam), int(sak), _dp(B), int(sbn), int(sbk), _dp(C), int(ldc), _dp(bias),
+                              _dp(C2), int(M), int(N), int(K), int(epi), int(ksplit), _dp(status), _stream(stream))
 
 
 def chem_boxes_set(ctx, boxes):
