@@ -249,6 +249,90 @@ int chem_tc_gemm(const float *A, int64_t sam, int64_t sak, const float *B, int64
                  float *C, int64_t ldc, const float *bias, float *C2, int32_t M, int32_t N, int32_t K,
                  int32_t epi, int32_t ksplit, int32_t *status, void *stream);
 
+/* ---------------------------------------------------------------------------------------------
+ * Learned surrogate of the chemistry step with a per-cell error gate.  The paper names machine
+ * learning for the chemistry as future work (Sec. 6); it has no counterpart there.  The network
+ * (compiled for ns = 9) maps x = (T, ln p, ln dt, ln(Y_k + 1e-6)), standardised, through four
+ * GELU layers of 128 to ns + 2 outputs: the standardised encodings a = asinh(u / 1e-8) of
+ * u_k = ln((Y1_k + 1e-6) / (max(Y_k, 0) + 1e-6)) and u_T = ln(T1 / T) for the state (Y1, T1)
+ * after dt (decoded with u clamped so that 0 <= Y1 <= 1 and T / 10 <= T1 <= 10 T), and an error head
+ * (log10 of the predicted relative error of the state the gate would write).  BF16 weights on
+ * the tensor cores, FP32 accumulation and FP32 master weights.  All state (weights, AdamW
+ * moments, normalisation, scratch) is owned by the context and freed by chem_destroy.
+ * --------------------------------------------------------------------------------------------- */
+
+/* Training configuration (chem_surrogate_train). */
+typedef struct {
+  int32_t epochs;       /* passes over the data set */
+  int32_t batch;        /* samples per step, a multiple of 128 (4096 by default) */
+  double lr;            /* peak AdamW learning rate, cosine-decayed to 0 over all steps */
+  double weight_decay;  /* decoupled weight decay */
+  double err_weight;    /* weight of the error-head term of the loss */
+  uint64_t seed;        /* shuffling seed */
+} chem_train_cfg;
+
+/* Create (or re-initialise) the context's surrogate: He-initialised weights from `seed`, zero
+ * AdamW moments, an empty training box (nothing is accepted until it is trained or loaded) and
+ * the conserved directions of the mechanism (the complement of the span of the reaction vectors
+ * W .* (nu_r - nu_f)).  CHEM_EUNSUPPORTED if ns != 9 or more than 4 directions are conserved. */
+int chem_surrogate_init(chem_ctx *ctx, uint64_t seed);
+
+/* Number of FP32 parameters (weights and biases of the five layers, W_l row-major [out][in]
+ * followed by b_l, layer by layer). */
+int chem_surrogate_nparams(void);
+
+/* Train on n samples (device arrays): X [n][12] rows (T [K], p [Pa], dt [s], Y_1..Y_9) and
+ * Yt [n][10] rows (Y1_1..Y1_9, T1), the state after dt (a standard deviation below 1e-12 is
+ * replaced by 1).  Sets the normalisation
+ * and the training box (range of every feature) from the data, then runs cfg->epochs epochs of shuffled full batches
+ * (forward and backward on the tensor cores, AdamW).  loss_per_epoch (host, [epochs], or null)
+ * receives the mean batch loss of each epoch.  Synchronous; returns CHEM_ECUDA if a
+ * tensor-core wait timed out. */
+int chem_surrogate_train(chem_ctx *ctx, const float *X, const float *Yt, int64_t n, const chem_train_cfg *cfg,
+                         float *loss_per_epoch, void *stream);
+
+/* Gradient of the training loss of one batch of n samples (n a multiple of 128; layouts as in
+ * chem_surrogate_train, normalisation as set by the last training or load) with respect to the
+ * FP32 parameters: grads (device, [nparams]) and the batch loss (device, [1]).  The loss is
+ * mean_b [ sum_j (o_bj - t_bj)^2 + err_weight (o_b,err - e*_b)^2 ], with t the standardised target
+ * encodings and e*_b = log10(E_b + 1e-12) held constant, E_b = max over species of
+ * |Y1'_k - Y1_k| / max(|Y1_k|, 1e-6) and |T1' - T1| / T1 for the corrected prediction (Y1', T1').  Synchronous. */
+int chem_surrogate_grads(chem_ctx *ctx, const float *X, const float *Yt, int32_t n, float err_weight,
+                         float *grads, float *loss, void *stream);
+
+/* Network outputs (standardised, [n][11], device) of the GEMM path for X [n][12] (device). */
+int chem_surrogate_forward(chem_ctx *ctx, const float *X, int32_t n, float *out, void *stream);
+
+/* Network outputs of the fused inference kernel of chem_advance_gated for n cells in the SoA
+ * layout of chem_advance (T, Y [9][ld], rho, e on the device; p is derived), [n][11] into out.
+ * The state is not modified.  Synchronous. */
+int chem_surrogate_infer(chem_ctx *ctx, const float *T, const float *Y, int64_t ld, const float *rho,
+                         const float *e, int64_t n, double dt, float *out, void *stream);
+
+/* Copy the FP32 parameters out to dst and/or in from src (host or device, [nparams]). */
+int chem_surrogate_params(chem_ctx *ctx, float *dst, const float *src, void *stream);
+
+/* Serialise the surrogate (versioned header, normalisation, FP32 parameters) into buf (host).
+ * With buf null only *size is set. */
+int chem_surrogate_save(chem_ctx *ctx, void *buf, size_t cap, size_t *size);
+
+/* Load a surrogate saved by chem_surrogate_save for the same mechanism shape. */
+int chem_surrogate_load(chem_ctx *ctx, const void *buf, size_t size);
+
+/* One chemistry step with the surrogate in front of the method.  Every cell first goes through
+ * the fused inference kernel; the gate accepts a cell only if (i) every feature lies within its
+ * range over the training set (widened by 1e-3 of the range) and Y >= -1e-10, (ii) the error head predicts a relative error <= gate_tol, and
+ * (iii) after a conservative correction of Y1 - Y (the smallest change, weighted by
+ * max(|Y1_k|, 1e-6), that keeps every conserved element mass) the mass fractions stay in
+ * [-1e-10, 1 + 1e-6], |sum (Y1 - Y)| <= 1e-7 and T(e, Y1) agrees with the network's T1 to 1e-4.  Accepted cells are written
+ * (T from e, p from the ideal gas law, substeps 0, accepted[i] = 1); all other cells
+ * (accepted[i] = 0) take the plain bulk / stiff path of chem_advance; the counters of
+ * chem_status cover those cells only.  *n_accepted (host, optional; the call then synchronizes)
+ * receives the number of accepted cells.  Arguments otherwise as chem_advance. */
+int chem_advance_gated(chem_ctx *ctx, float *T, float *p, float *Y, int64_t ld, const float *rho,
+                       const float *e, int64_t n, double dt, double gate_tol, uint8_t *accepted,
+                       int32_t *substeps, int64_t *n_accepted, void *stream);
+
 /* Synchronize `stream` and return the counters of the last advance call on this context. */
 int chem_status(chem_ctx *ctx, void *stream, chem_stats *out);
 

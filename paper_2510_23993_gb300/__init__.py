@@ -59,6 +59,11 @@ class chem_tune_result(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class chem_train_cfg(ctypes.Structure):
+    _fields_ = [("epochs", ctypes.c_int32), ("batch", ctypes.c_int32), ("lr", ctypes.c_double),
+                ("weight_decay", ctypes.c_double), ("err_weight", ctypes.c_double), ("seed", ctypes.c_uint64)]
+
+
 class chem_stats(ctypes.Structure):
     _fields_ = [("ncell", ctypes.c_int64), ("nskipped", ctypes.c_int64), ("nbulk", ctypes.c_int64),
                 ("nqueued", ctypes.c_int64), ("nfailed", ctypes.c_int64), ("ninvalid", ctypes.c_int64),
@@ -114,6 +119,21 @@ def lib():
         L.chem_tune.restype = i32
         L.chem_tc_gemm.argtypes = [vp, i64, i64, vp, i64, i64, vp, i64, vp, vp, i32, i32, i32, i32, i32, vp, vp]
         L.chem_tc_gemm.restype = i32
+        u64, szt = ctypes.c_uint64, ctypes.c_size_t
+        L.chem_surrogate_init.argtypes = [vp, u64]
+        L.chem_surrogate_nparams.argtypes = []
+        L.chem_surrogate_train.argtypes = [vp, vp, vp, i64, _P(chem_train_cfg), vp, vp]
+        L.chem_surrogate_grads.argtypes = [vp, vp, vp, i32, ctypes.c_float, vp, vp, vp]
+        L.chem_surrogate_forward.argtypes = [vp, vp, i32, vp, vp]
+        L.chem_surrogate_infer.argtypes = [vp, vp, vp, i64, vp, vp, i64, d, vp, vp]
+        L.chem_surrogate_params.argtypes = [vp, vp, vp, vp]
+        L.chem_surrogate_save.argtypes = [vp, vp, szt, _P(szt)]
+        L.chem_surrogate_load.argtypes = [vp, vp, szt]
+        L.chem_advance_gated.argtypes = [vp, vp, vp, vp, i64, vp, vp, i64, d, d, vp, vp, _P(i64), vp]
+        for name in ("chem_surrogate_init", "chem_surrogate_nparams", "chem_surrogate_train", "chem_surrogate_grads",
+                     "chem_surrogate_forward", "chem_surrogate_infer", "chem_surrogate_params", "chem_surrogate_save",
+                     "chem_surrogate_load", "chem_advance_gated"):
+            getattr(L, name).restype = i32
         L.chem_strerror.argtypes = [i32]
         L.chem_strerror.restype = ctypes.c_char_p
         for name in ("chem_init", "chem_set_params", "chem_advance", "chem_advance_f64", "chem_advance_host",
@@ -216,6 +236,56 @@ def chem_advance_noalloc(mech, params, T, p, Y, ld, rho, e, n, dt, substeps, sta
 def chem_tc_gemm(A, sam, sak, B, sbn, sbk, C, ldc, bias, C2, M, N, K, epi, ksplit, status, stream=None):
     return lib().chem_tc_gemm(_dp(A), int(sam), int(sak), _dp(B), int(sbn), int(sbk), _dp(C), int(ldc), _dp(bias),
                               _dp(C2), int(M), int(N), int(K), int(epi), int(ksplit), _dp(status), _stream(stream))
+
+
+def chem_surrogate_init(ctx, seed=0):
+    return lib().chem_surrogate_init(ctx, int(seed))
+
+
+def chem_surrogate_nparams():
+    return lib().chem_surrogate_nparams()
+
+
+def chem_surrogate_train(ctx, X, Yt, n, cfg, loss_per_epoch=None, stream=None):
+    """X [n][12] = (T, p, dt, Y[9]), Yt [n][10] = (dY[9], dT), device; loss_per_epoch: ctypes float array."""
+    return lib().chem_surrogate_train(ctx, _dp(X), _dp(Yt), int(n), ctypes.byref(cfg), loss_per_epoch,
+                                      _stream(stream))
+
+
+def chem_surrogate_grads(ctx, X, Yt, n, err_weight, grads, loss, stream=None):
+    return lib().chem_surrogate_grads(ctx, _dp(X), _dp(Yt), int(n), float(err_weight), _dp(grads), _dp(loss),
+                                      _stream(stream))
+
+
+def chem_surrogate_forward(ctx, X, n, out, stream=None):
+    return lib().chem_surrogate_forward(ctx, _dp(X), int(n), _dp(out), _stream(stream))
+
+
+def chem_surrogate_infer(ctx, T, Y, ld, rho, e, n, dt, out, stream=None):
+    return lib().chem_surrogate_infer(ctx, _dp(T), _dp(Y), int(ld), _dp(rho), _dp(e), int(n), float(dt), _dp(out),
+                                      _stream(stream))
+
+
+def chem_surrogate_params(ctx, dst=None, src=None, stream=None):
+    return lib().chem_surrogate_params(ctx, _dp(dst), _dp(src), _stream(stream))
+
+
+def chem_surrogate_save(ctx):
+    size = ctypes.c_size_t(0)
+    _check(lib().chem_surrogate_save(ctx, None, 0, ctypes.byref(size)), "chem_surrogate_save")
+    buf = ctypes.create_string_buffer(size.value)
+    _check(lib().chem_surrogate_save(ctx, buf, size.value, ctypes.byref(size)), "chem_surrogate_save")
+    return buf.raw
+
+
+def chem_surrogate_load(ctx, blob):
+    return lib().chem_surrogate_load(ctx, blob, len(blob))
+
+
+def chem_advance_gated(ctx, T, p, Y, ld, rho, e, n, dt, gate_tol, accepted, substeps, n_accepted=None, stream=None):
+    return lib().chem_advance_gated(ctx, _dp(T), _dp(p), _dp(Y), int(ld), _dp(rho), _dp(e), int(n), float(dt),
+                                    float(gate_tol), _dp(accepted), _dp(substeps),
+                                    ctypes.byref(n_accepted) if n_accepted is not None else None, _stream(stream))
 
 
 def chem_boxes_set(ctx, boxes):
@@ -339,3 +409,47 @@ class Context:
 
     def launch_boxes(self, stream=None):
         _check(chem_boxes_launch(self.handle, stream), "chem_boxes_launch")
+
+    # ---- surrogate
+    def surrogate_init(self, seed=0):
+        _check(chem_surrogate_init(self.handle, seed), "chem_surrogate_init")
+
+    def surrogate_train(self, X, Yt, epochs=20, batch=4096, lr=1e-3, weight_decay=1e-5, err_weight=0.1, seed=0,
+                        stream=None):
+        """Train on device arrays X [n][12] = (T, p, dt, Y[9]) and Yt [n][10] = (dY[9], dT); returns the
+        mean loss of each epoch."""
+        for t in (X, Yt):
+            if not t.is_cuda or not t.is_contiguous() or t.dtype.itemsize != 4:
+                raise ValueError("X and Yt must be contiguous float32 CUDA tensors")
+        cfg = chem_train_cfg(int(epochs), int(batch), float(lr), float(weight_decay), float(err_weight), int(seed))
+        losses = (ctypes.c_float * max(int(epochs), 1))()
+        _check(chem_surrogate_train(self.handle, X, Yt, X.shape[0], cfg, losses, stream), "chem_surrogate_train")
+        return list(losses)[:int(epochs)]
+
+    def surrogate_grads(self, X, Yt, err_weight, grads, loss, stream=None):
+        _check(chem_surrogate_grads(self.handle, X, Yt, X.shape[0], err_weight, grads, loss, stream),
+               "chem_surrogate_grads")
+
+    def surrogate_forward(self, X, out, stream=None):
+        _check(chem_surrogate_forward(self.handle, X, X.shape[0], out, stream), "chem_surrogate_forward")
+
+    def surrogate_infer(self, T, Y, rho, e, dt, out, stream=None):
+        n = self._check_state(T, Y, rho, e, out)
+        _check(chem_surrogate_infer(self.handle, T, Y, Y.stride(0), rho, e, n, dt, out, stream), "chem_surrogate_infer")
+
+    def surrogate_params(self, dst=None, src=None, stream=None):
+        _check(chem_surrogate_params(self.handle, dst, src, stream), "chem_surrogate_params")
+
+    def surrogate_save(self):
+        return chem_surrogate_save(self.handle)
+
+    def surrogate_load(self, blob):
+        _check(chem_surrogate_load(self.handle, blob), "chem_surrogate_load")
+
+    def advance_gated(self, T, p, Y, rho, e, dt, gate_tol, accepted, substeps, stream=None):
+        """One step with the surrogate in front of the method; returns the number of accepted cells."""
+        n = self._check_state(T, Y, p, rho, e, substeps, accepted)
+        na = ctypes.c_int64(0)
+        _check(chem_advance_gated(self.handle, T, p, Y, Y.stride(0), rho, e, n, dt, gate_tol, accepted, substeps, na,
+                                  stream), "chem_advance_gated")
+        return int(na.value)

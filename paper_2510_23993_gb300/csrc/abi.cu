@@ -10,6 +10,13 @@
 #include "chem_device.cuh"
 #include "internal.h"
 
+namespace chem {
+namespace sg {
+struct State;
+}
+void surrogate_release(sg::State* s);   // surrogate.cu
+}  // namespace chem
+
 using namespace chem;
 
 struct chem_ctx {
@@ -38,6 +45,10 @@ struct chem_ctx {
   // staging buffers of chem_advance_host (allocated on its first use)
   float* hbuf = nullptr;
   int* hsub = nullptr;
+  // host copies of the stoichiometry (the surrogate's conservation constraints)
+  std::vector<double> W;
+  std::vector<int8_t> nu_f, nu_r;
+  chem::sg::State* sg = nullptr;   // surrogate (surrogate.cu), created by chem_surrogate_init
 };
 
 namespace {
@@ -229,7 +240,7 @@ KParams kparams(const chem_params& p) {
 
 template <typename S>
 int advance_impl(chem_ctx* ctx, S* T, S* p, S* Y, int64_t ld, const S* rho, const S* e, int64_t n, double dt,
-                 int32_t* substeps, cudaStream_t st) {
+                 int32_t* substeps, cudaStream_t st, const unsigned char* skip = nullptr) {
   if (!ctx || n < 0 || !(dt > 0) || !std::isfinite(dt)) return CHEM_EINVAL;
   if (n > ctx->max_cells) return CHEM_ENOMEM;
   if (n > 0 && (!T || !Y || !rho || !e || !substeps || ld < n)) return CHEM_EINVAL;
@@ -258,6 +269,7 @@ int advance_impl(chem_ctx* ctx, S* T, S* p, S* Y, int64_t ld, const S* rho, cons
     a.boxes = nullptr;
     a.box_off = nullptr;
     a.nbox = 0;
+    a.skip = skip;
     const bool order = (ctx->prm.flags & (CHEM_FLAG_ORDER_RATE | CHEM_FLAG_ORDER_PREV)) != 0;
     a.qkey = order ? ctx->qkey : nullptr;
     long long want = (n + kBulkBlock - 1) / kBulkBlock;
@@ -313,6 +325,26 @@ int occupancy_stiff(const chem_ctx* c) {
   if (stiff_occupancy(c->ns, c->blob_bytes, &b) != 0 || b < 1) b = 1;
   return b;
 }
+// surrogate state and the mechanism data it needs (surrogate.cu)
+sg::State* ctx_surrogate(chem_ctx* c) { return c->sg; }
+void ctx_set_surrogate(chem_ctx* c, sg::State* s) { c->sg = s; }
+void ctx_mech_host(const chem_ctx* c, int* ns, int* nr, const double** W, const int8_t** nuf, const int8_t** nur) {
+  *ns = c->ns;
+  *nr = c->nr;
+  *W = c->W.data();
+  *nuf = c->nu_f.data();
+  *nur = c->nu_r.data();
+}
+const unsigned char* ctx_blob(const chem_ctx* c, unsigned* bytes) {
+  *bytes = c->blob_bytes;
+  return c->blob;
+}
+int ctx_device(const chem_ctx* c) { return c->dev; }
+// chem_advance with a skip mask: cells with skip[i] != 0 are left as they are
+int ctx_advance_skip(chem_ctx* c, float* T, float* p, float* Y, int64_t ld, const float* rho, const float* e, int64_t n,
+                     double dt, int32_t* substeps, const unsigned char* skip, cudaStream_t st) {
+  return advance_impl<float>(c, T, p, Y, ld, rho, e, n, dt, substeps, st, skip);
+}
 }  // namespace chem
 
 extern "C" {
@@ -348,6 +380,9 @@ int chem_init(const chem_mechanism* mech, const chem_params* params, int64_t max
   c->max_cells = max_cells;
   c->ns = mech->ns;
   c->nr = mech->nr;
+  c->W.assign(mech->W, mech->W + mech->ns);
+  c->nu_f.assign(mech->nu_f, mech->nu_f + static_cast<size_t>(mech->nr) * mech->ns);
+  c->nu_r.assign(mech->nu_r, mech->nu_r + static_cast<size_t>(mech->nr) * mech->ns);
   std::vector<unsigned char> blob;
   pack_mechanism(mech, blob, &c->ntb);
   c->blob_bytes = static_cast<unsigned>(blob.size());
@@ -403,6 +438,7 @@ void chem_destroy(chem_ctx* ctx) {
   if (ctx->graph) cudaGraphDestroy(ctx->graph);
   cudaFree(ctx->boxes);
   cudaFree(ctx->box_off);
+  surrogate_release(ctx->sg);
   delete ctx;
 }
 

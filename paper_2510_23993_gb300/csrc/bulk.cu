@@ -32,7 +32,7 @@ __global__ void __launch_bounds__(kBulkBlock) bulk_kernel(const AdvanceArgs<S> a
     const long long g = base + lane;
     bool enqueue = false;
     int bucket = 0;
-    if (g < a.n) {
+    if (g < a.n && !(a.skip && a.skip[g])) {
       const CellRef<S> cr = locate(a, soff, g);
       const long long i = cr.i;
       const double dt = cr.dt;

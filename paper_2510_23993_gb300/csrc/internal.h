@@ -53,6 +53,8 @@ struct AdvanceArgs {
   const DevBox<S>* boxes;        // box table (nbox > 0): global cell g lives in the box whose
   const int* box_off;            //   [off_b, off_b + n_b) range; box_off[b] = off_b, b <= nbox
   int nbox;                      // 0: flat arrays T, p, Y, rho, e, substeps of n cells, step dt
+  const unsigned char* skip;     // [n] or null: cells with skip[g] != 0 are left untouched (their
+                                 //   step was taken elsewhere, e.g. by the surrogate)
 };
 
 constexpr int kMaxBoxes = 4096;

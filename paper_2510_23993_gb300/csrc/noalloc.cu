@@ -262,6 +262,7 @@ extern "C" int chem_advance_noalloc(const chem_mechanism* mech, const chem_param
     a.boxes = nullptr;
     a.box_off = nullptr;
     a.nbox = 0;
+    a.skip = nullptr;
     int bpsm = 1, spsm = 1;
     if (bulk_occupancy(mech->ns, false, bytes, &bpsm) != 0 || bpsm < 1) bpsm = 1;
     if (stiff_occupancy(mech->ns, bytes, &spsm) != 0 || spsm < 1) spsm = 1;

@@ -1,0 +1,1140 @@
+// surrogate.cu -- a learned shortcut of the chemistry step with a per-cell error gate.
+//
+// Network: features x = (T, ln p, ln dt, ln(Y_k + eps)) (ns + 3 inputs, standardised) -> 4 hidden
+// layers of 128 with GELU -> ns + 2 outputs: the standardised encodings a_j of the changes of
+// Y_1..Y_ns and T over dt, and an "error head" that predicts log10 of the relative error of the
+// state the gate would write.  The changes are encoded as
+//     u_k = ln((Y_k + dY_k + eps) / (Y_k + eps)),   u_T = ln((T + dT) / T),   a = asinh(u / u0),
+// so that an error da in the network output is an error of ~ max(|u|, u0) da in u, i.e. a
+// relative error of the new Y_k + eps: the accuracy the 1e-4 parity bar asks for on Y_k >= 1e-6
+// (and 1e-10 absolute below) is reached on every cell whose change is small enough, whatever
+// its size class.  Weights are FP32 masters, rounded to BF16 for every tensor-core product
+// (FP32 accumulation in TMEM).
+//
+// Training (chem_surrogate_train): mini-batch AdamW with cosine learning-rate decay; forward and
+// backward are tensor-core GEMMs of mlp.cu (forward X W^T, backward-data dZ W, backward-weight
+// dZ^T A with the batch split over CTAs) plus elementwise kernels (encoding, loss, GELU
+// derivative, bias gradients, optimiser).  Inference in chem_advance_gated is one fused
+// persistent kernel: all BF16 weights resident in shared memory, 128 cells per tile, the
+// activations of a tile kept in shared memory and TMEM between layers, followed by the gate:
+//   (i)   every feature inside its range over the training set (widened by 1e-3 of the range),
+//         and Y >= -atol,
+//   (ii)  predicted log10 error at most log10(gate_tol),
+//   (iii) dY made conservative (weighted least-squares correction onto the span of the reaction
+//         vectors, weights set by the tolerance scale so that major species absorb it), then
+//         |sum_k dY_k| <= 1e-7, 0 - atol <= Y + dY <= 1 + 1e-6, and the network's dT consistent
+//         with T(e, Y + dY) to 1e-4 relative.
+// Accepted cells are written (T from e at the new Y, p from the ideal gas law, substeps 0); the
+// others go through the bulk and stiff kernels unchanged.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <random>
+#include <vector>
+
+#include "../../include/chem.h"
+#include "chem_device.cuh"
+#include "internal.h"
+#include "tc.cuh"
+
+namespace chem {
+
+// from mlp.cu
+struct GemmArgs {
+  const float* A;
+  long long sam, sak;
+  const float* B;
+  long long sbn, sbk;
+  float* C;
+  long long ldc;
+  float* C2;
+  const float* bias;
+  int M, N, K, k_per_split, epi;
+  int* status;
+};
+int launch_gemm(const GemmArgs& g, int ksplit, cudaStream_t s);
+
+namespace sg {
+
+constexpr int kH = 128;        // hidden width
+constexpr int kNS = 9;         // species of the compiled surrogate
+constexpr int kNIn = kNS + 3;  // inputs
+constexpr int kNOut = kNS + 2; // outputs: a(dY), a(dT), log10 error
+constexpr int kNTgt = kNS + 1; // regression targets
+constexpr int kKIn = 16;       // input K padded for the tensor core
+constexpr int kNOutPad = 16;   // output N padded
+constexpr int kRaw = 2 * kNS + 2;   // raw per-sample record of a batch: Y0[ns], T0, Y1[ns], T1
+constexpr int kMaxCons = 4;    // conserved directions (elements) supported
+constexpr float kEps = 1e-6f;  // Y floor of the log features and of the relative error
+constexpr float kU0 = 1e-8f;   // linear range of the asinh compression of u
+
+// flat parameter offsets (FP32 masters); W_l is [out][in] row-major
+constexpr int oW1 = 0, oB1 = oW1 + kH * kNIn;
+constexpr int oW2 = oB1 + kH, oB2 = oW2 + kH * kH;
+constexpr int oW3 = oB2 + kH, oB3 = oW3 + kH * kH;
+constexpr int oW4 = oB3 + kH, oB4 = oW4 + kH * kH;
+constexpr int oW5 = oB4 + kH, oB5 = oW5 + kNOut * kH;
+constexpr int kNParams = oB5 + kNOut;
+
+// normalisation, training box and conservation constraints (FP32)
+struct Norm {
+  float mu_x[kNIn], sd_x[kNIn];
+  float mu_y[kNTgt], sd_y[kNTgt];
+  float lo_x[kNIn], hi_x[kNIn];    // training box of the (unstandardised) features
+  float C[kMaxCons][kNS];          // orthonormal basis of the directions no reaction moves Y in
+  int ncons;
+  int pad[3];
+};
+
+// packed inference blob (shared-memory image): BF16 weights in the K-major core-matrix layout
+// followed by FP32 biases and the Norm block
+constexpr int bW1 = 0;                          // 128 x 16
+constexpr int bW2 = bW1 + kH * kKIn * 2;        // 128 x 128
+constexpr int bW3 = bW2 + kH * kH * 2;
+constexpr int bW4 = bW3 + kH * kH * 2;
+constexpr int bW5 = bW4 + kH * kH * 2;          // 16 x 128
+constexpr int bBias = bW5 + kNOutPad * kH * 2;  // b1..b4 [4][128], b5 [16]
+constexpr int bNorm = bBias + (4 * kH + kNOutPad) * 4;
+constexpr int kBlobBytes = ((bNorm + static_cast<int>(sizeof(Norm))) + 15) & ~15;
+
+__device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad(float x) {
+  return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) + x * 0.3989422804014327f * expf(-0.5f * x * x);
+}
+
+// ------------------------------------------------------------------ encoding (shared by training and inference)
+
+__device__ __forceinline__ void features(float T, float p, float lndt, const float* y, float* x) {
+  x[0] = T;
+  x[1] = logf(p);
+  x[2] = lndt;
+#pragma unroll
+  for (int k = 0; k < kNS; ++k) x[3 + k] = logf(fmaxf(y[k], 0.0f) + kEps);
+}
+
+// u = ln((x1 + c) / (x0 + c)) without cancellation: log1p of the (exact, nearby) difference when
+// the ratio is near 1, the difference of logarithms otherwise (c = eps for species, 0 for T)
+__device__ __forceinline__ float log_ratio(float x1, float x0, float c) {
+  const float base = x0 + c;
+  const float d = x1 - x0;
+  return fabsf(d) < 0.5f * base ? log1pf(d / base) : logf(fmaxf(x1 + c, 1e-30f)) - logf(base);
+}
+__device__ __forceinline__ float encode(float u) { return asinhf(u / kU0); }
+// u of a network output a, clamped to [u_lo, u_hi]
+__device__ __forceinline__ float decode_u(float a, float u_lo, float u_hi) {
+  return fminf(fmaxf(kU0 * sinhf(fminf(fmaxf(a, -60.0f), 60.0f)), u_lo), u_hi);
+}
+// x1 = (x0 + c) e^u - c, from x0 plus an expm1 increment for small |u| (no cancellation), from
+// the exponential for large |u|
+__device__ __forceinline__ float apply_u(float x0, float c, float u) {
+  return fabsf(u) < 0.5f ? x0 + (x0 + c) * expm1f(u) : (x0 + c) * expf(u) - c;
+}
+constexpr float kLnEps = -13.815510557964274f;   // ln(1e-6)
+constexpr float kLnTen = 2.302585092994046f;
+
+// conservative correction of the new mass fractions y1 (change dY = y1 - y0): the smallest
+// change in the norm sum_k (delta_k / w_k)^2, w_k = max(|y1_k|, eps), that makes C dY = 0.  With
+// B = C diag(w) and B^T = Q R (modified Gram-Schmidt, FP64), delta = -diag(w) Q R^{-T} (C dY).
+__device__ __forceinline__ void conserve(const Norm& nm, const float* y0, float* y1) {
+  const int m = nm.ncons;
+  if (m <= 0) return;
+  double w[kNS], q[kMaxCons][kNS], R[kMaxCons][kMaxCons], y[kMaxCons];
+#pragma unroll
+  for (int k = 0; k < kNS; ++k) w[k] = fmax(fabs(static_cast<double>(y1[k])), static_cast<double>(kEps));
+#pragma unroll
+  for (int i = 0; i < kMaxCons; ++i) {
+    y[i] = 0.0;
+    if (i >= m) continue;
+    double r = 0.0;
+#pragma unroll
+    for (int k = 0; k < kNS; ++k) {
+      q[i][k] = w[k] * nm.C[i][k];
+      r += nm.C[i][k] * (static_cast<double>(y1[k]) - static_cast<double>(y0[k]));
+    }
+#pragma unroll
+    for (int j = 0; j < i; ++j) {
+      double d = 0.0;
+#pragma unroll
+      for (int k = 0; k < kNS; ++k) d += q[j][k] * q[i][k];
+      R[j][i] = d;
+#pragma unroll
+      for (int k = 0; k < kNS; ++k) q[i][k] -= d * q[j][k];
+    }
+    double nrm = 0.0;
+#pragma unroll
+    for (int k = 0; k < kNS; ++k) nrm += q[i][k] * q[i][k];
+    nrm = sqrt(nrm);
+    R[i][i] = nrm;
+    const double inv = nrm > 1e-300 ? 1.0 / nrm : 0.0;
+#pragma unroll
+    for (int k = 0; k < kNS; ++k) q[i][k] *= inv;
+    // forward substitution of R^T y = C dY (a degenerate direction contributes nothing)
+#pragma unroll
+    for (int j = 0; j < i; ++j) r -= R[j][i] * y[j];
+    y[i] = r * inv;
+  }
+#pragma unroll
+  for (int k = 0; k < kNS; ++k) {
+    double z = 0.0;
+#pragma unroll
+    for (int i = 0; i < kMaxCons; ++i)
+      if (i < m) z += q[i][k] * y[i];
+    y1[k] = static_cast<float>(static_cast<double>(y1[k]) - w[k] * z);
+  }
+}
+
+// network outputs o (standardised) -> conservative new mass fractions y1 and temperature T1
+__device__ __forceinline__ void decode_state(const Norm& nm, const float* o, const float* y0, float T0, float* y1,
+                                             float* T1) {
+#pragma unroll
+  for (int k = 0; k < kNS; ++k) {
+    const float y0c = fmaxf(y0[k], 0.0f);
+    const float lb = logf(y0c + kEps);
+    const float u = decode_u(o[k] * nm.sd_y[k] + nm.mu_y[k], kLnEps - lb, log1pf(kEps) - lb);
+    y1[k] = apply_u(y0c, kEps, u);
+  }
+  *T1 = apply_u(T0, 0.0f, decode_u(o[kNS] * nm.sd_y[kNS] + nm.mu_y[kNS], -kLnTen, kLnTen));
+  conserve(nm, y0, y1);
+}
+
+// ------------------------------------------------------------------ training kernels
+
+// gather + encode a batch: Xn [B][16] (standardised features, zero padded), Tn [B][10]
+// (standardised target encodings, if Yt), Raw [B][20] = (Y0, T0, Y1, T1).  X rows are
+// (T, p, dt, Y0[ns]); Yt rows are (Y1[ns], T1), the state after dt.
+__device__ __forceinline__ void target_encodings(const float* xr, const float* yr, float* a) {
+#pragma unroll
+  for (int k = 0; k < kNS; ++k) a[k] = encode(log_ratio(yr[k], fmaxf(xr[3 + k], 0.0f), kEps));
+  a[kNS] = encode(log_ratio(yr[kNS], xr[0], 0.0f));
+}
+
+__global__ void batch_kernel(const float* X, const float* Yt, const int* idx, int B, const Norm* nm, float* Xn,
+                             float* Tn, float* Raw) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  const long long i = idx ? idx[b] : b;
+  const float* xr = X + i * kNIn;
+  float y0[kNS], x[kNIn];
+#pragma unroll
+  for (int k = 0; k < kNS; ++k) y0[k] = xr[3 + k];
+  features(xr[0], xr[1], logf(xr[2]), y0, x);
+#pragma unroll
+  for (int j = 0; j < kKIn; ++j) Xn[b * kKIn + j] = j < kNIn ? (x[j] - nm->mu_x[j]) / nm->sd_x[j] : 0.0f;
+  if (!Yt) return;
+  const float* yr = Yt + i * kNTgt;
+  float a[kNTgt];
+  target_encodings(xr, yr, a);
+#pragma unroll
+  for (int j = 0; j < kNTgt; ++j) Tn[b * kNTgt + j] = (a[j] - nm->mu_y[j]) / nm->sd_y[j];
+#pragma unroll
+  for (int k = 0; k < kNS; ++k) {
+    Raw[b * kRaw + k] = y0[k];
+    Raw[b * kRaw + kNS + 1 + k] = yr[k];
+  }
+  Raw[b * kRaw + kNS] = xr[0];
+  Raw[b * kRaw + 2 * kNS + 1] = yr[kNS];
+}
+
+// relative error of the state the gate would write: max over species of |Y1' - Y1| / max(|Y1|, eps)
+// and |T1' - T1| / T1
+__device__ __forceinline__ float state_error(const Norm& nm, const float* o, const float* raw) {
+  float y1[kNS], T1;
+  decode_state(nm, o, raw, raw[kNS], y1, &T1);
+  float E = 0.0f;
+#pragma unroll
+  for (int k = 0; k < kNS; ++k) {
+    const float t = raw[kNS + 1 + k];
+    E = fmaxf(E, fabsf(y1[k] - t) / fmaxf(fabsf(t), kEps));
+  }
+  const float Tt = raw[2 * kNS + 1];
+  return fmaxf(E, fabsf(T1 - Tt) / Tt);
+}
+
+// loss and its gradient at the output layer: MSE of the standardised target encodings plus
+// err_weight * (o_err - e*)^2 with e* = log10(state error + 1e-12) (no gradient through e*)
+__global__ void loss_kernel(const float* Z5, const float* Tn, const float* Raw, int B, const Norm* nm,
+                            float err_weight, float* dZ5, float* loss) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  float l = 0.0f;
+  if (b < B) {
+    const float* o = Z5 + b * kNOut;
+    for (int j = 0; j < kNTgt; ++j) {
+      const float d = o[j] - Tn[b * kNTgt + j];
+      l += d * d;
+      dZ5[b * kNOut + j] = 2.0f * d / B;
+    }
+    const float es = log10f(state_error(*nm, o, Raw + b * kRaw) + 1e-12f);
+    const float de = o[kNS + 1] - es;
+    l += err_weight * de * de;
+    dZ5[b * kNOut + kNS + 1] = 2.0f * err_weight * de / B;
+  }
+  __shared__ float red[256];
+  red[threadIdx.x] = l;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) atomicAdd(loss, red[0] / B);
+}
+
+__global__ void gelu_back_kernel(const float* dA, const float* Z, float* dZ, long long n) {
+  const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i < n) dZ[i] = dA[i] * gelu_grad(Z[i]);
+}
+
+// column sums of dZ [B][N] into db[N] (atomic)
+__global__ void bias_grad_kernel(const float* dZ, int B, int N, float* db) {
+  const int n = threadIdx.x;
+  if (n >= N) return;
+  float s = 0.0f;
+  for (int b = blockIdx.x; b < B; b += gridDim.x) s += dZ[static_cast<long long>(b) * N + n];
+  atomicAdd(&db[n], s);
+}
+
+__global__ void adamw_kernel(float* w, const float* g, float* m, float* v, int n, float lr, float b1, float b2,
+                             float eps, float wd, float c1, float c2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float gi = g[i];
+  const float mi = b1 * m[i] + (1.0f - b1) * gi;
+  const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  w[i] -= lr * ((mi / c1) / (sqrtf(vi / c2) + eps) + wd * w[i]);
+}
+
+// dataset statistics of the features and of the target encodings (sum, sum of squares) and the
+// range of every feature as order-preserving integer keys
+__device__ __forceinline__ unsigned int order_key(float v) {
+  const unsigned int b = __float_as_uint(v);
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+__global__ void stats_kernel(const float* X, const float* Yt, long long n, double* acc, unsigned int* mm) {
+  constexpr int NT = kNIn + kNTgt;
+  double s[NT], q[NT];
+  for (int j = 0; j < NT; ++j) s[j] = q[j] = 0.0;
+  unsigned int lo[kNIn], hi[kNIn];
+  for (int j = 0; j < kNIn; ++j) {
+    lo[j] = 0xFFFFFFFFu;
+    hi[j] = 0u;
+  }
+  for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+       i += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const float* xr = X + i * kNIn;
+    const float* yr = Yt + i * kNTgt;
+    float y0[kNS], x[kNIn], a[kNTgt];
+    for (int k = 0; k < kNS; ++k) y0[k] = xr[3 + k];
+    features(xr[0], xr[1], logf(xr[2]), y0, x);
+    target_encodings(xr, yr, a);
+    for (int j = 0; j < kNIn; ++j) {
+      s[j] += x[j];
+      q[j] += static_cast<double>(x[j]) * x[j];
+    }
+    for (int j = 0; j < kNTgt; ++j) {
+      s[kNIn + j] += a[j];
+      q[kNIn + j] += static_cast<double>(a[j]) * a[j];
+    }
+    for (int j = 0; j < kNIn; ++j) {
+      lo[j] = min(lo[j], order_key(x[j]));
+      hi[j] = max(hi[j], order_key(x[j]));
+    }
+  }
+  for (int j = 0; j < NT; ++j) {
+    atomicAdd(&acc[j], s[j]);
+    atomicAdd(&acc[NT + j], q[j]);
+  }
+  for (int j = 0; j < kNIn; ++j) {
+    atomicMin(&mm[j], lo[j]);
+    atomicMax(&mm[kNIn + j], hi[j]);
+  }
+}
+
+// ------------------------------------------------------------------ inference blob
+
+// BF16 weights into the shared-memory image (K-major core matrices), biases and Norm after them
+__global__ void pack_blob_kernel(const float* params, const Norm* nm, unsigned char* blob) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nt = gridDim.x * blockDim.x;
+  auto put = [&](int base, const float* W, int rows, int rows_valid, int K, int K_valid) {
+    for (int i = t; i < rows * K; i += nt) {
+      const int r = i / K, k = i % K;
+      const float v = (r < rows_valid && k < K_valid) ? W[r * K_valid + k] : 0.0f;
+      *reinterpret_cast<__nv_bfloat16*>(blob + base + tc::kmajor_offset(r, k, K)) = __float2bfloat16_rn(v);
+    }
+  };
+  put(bW1, params + oW1, kH, kH, kKIn, kNIn);
+  put(bW2, params + oW2, kH, kH, kH, kH);
+  put(bW3, params + oW3, kH, kH, kH, kH);
+  put(bW4, params + oW4, kH, kH, kH, kH);
+  put(bW5, params + oW5, kNOutPad, kNOut, kH, kH);
+  float* bias = reinterpret_cast<float*>(blob + bBias);
+  for (int i = t; i < 4 * kH + kNOutPad; i += nt) {
+    float v;
+    if (i < 4 * kH) {
+      const int l = i / kH, n = i % kH;
+      const int ob = l == 0 ? oB1 : (l == 1 ? oB2 : (l == 2 ? oB3 : oB4));
+      v = params[ob + n];
+    } else {
+      const int n = i - 4 * kH;
+      v = n < kNOut ? params[oB5 + n] : 0.0f;
+    }
+    bias[i] = v;
+  }
+  const int* src = reinterpret_cast<const int*>(nm);
+  int* dst = reinterpret_cast<int*>(blob + bNorm);
+  for (int i = t; i < static_cast<int>(sizeof(Norm) / 4); i += nt) dst[i] = src[i];
+}
+
+// ------------------------------------------------------------------ fused inference + gate
+
+struct GatedArgs {
+  const unsigned char* mech;      // chemistry tables (T(e) for the gate)
+  unsigned mech_bytes;
+  const unsigned char* sblob;     // packed surrogate image
+  float* T;
+  float* p;
+  float* Y;
+  long long ld;
+  const float* rho;
+  const float* e;
+  long long n;
+  double dt;
+  float gate_log10, atol;
+  unsigned char* accepted;
+  int* substeps;
+  unsigned long long* n_accepted;
+  int* status;
+  float* out;                     // optional raw outputs [n][kNOut] (testing), or null
+};
+
+__global__ void __launch_bounds__(128, 1) surrogate_infer_kernel(const GatedArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ uint64_t bar_s, bar_m, bar_mma;
+  __shared__ uint32_t s_taddr;
+  // shared-memory image: [surrogate blob][mechanism blob][X tile 128x16][H tile 128x128]
+  unsigned char* sS = smem;
+  unsigned char* sM = smem + ((kBlobBytes + 1023) & ~1023);
+  unsigned char* sX = sM + ((a.mech_bytes + 1023) & ~1023);
+  unsigned char* sHt = sX + kH * kKIn * 2;
+  if (!stage_to_smem(sS, a.sblob, kBlobBytes, &bar_s, a.status)) return;
+  if (!stage_to_smem(sM, a.mech, a.mech_bytes, &bar_m, a.status)) return;
+  const MechView m = make_view(sM);
+  const Norm& nm = *reinterpret_cast<const Norm*>(sS + bNorm);
+  const float* bias = reinterpret_cast<const float*>(sS + bBias);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, t = threadIdx.x;
+  if (warp == 0) tc::tmem_alloc(&s_taddr, 128);
+  if (t == 0) tc::mbar_init(&bar_mma, 1);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t taddr = s_taddr;
+  const uint32_t lane_addr = taddr + (static_cast<uint32_t>(warp * 32) << 16);
+  uint32_t phase = 0;
+  bool ok = true;
+  unsigned long long c_acc = 0;
+  const float lndt = static_cast<float>(log(a.dt));
+  const long long ntiles = (a.n + kH - 1) / kH;
+  for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+    const long long i = tile * kH + t;
+    const bool valid = i < a.n;
+    float y[kNS], T = 0.0f, rho = 1.0f, e = 0.0f;
+    float x[kNIn];
+    bool inbox = valid;
+    if (valid) {
+      T = a.T[i];
+      rho = a.rho[i];
+      e = a.e[i];
+      double sw = 0.0;
+#pragma unroll
+      for (int k = 0; k < kNS; ++k) {
+        y[k] = a.Y[k * a.ld + i];
+        sw += static_cast<double>(y[k]) * m.e64[k * 8 + 6];
+        inbox = inbox && y[k] >= -a.atol;
+      }
+      const float p = static_cast<float>(static_cast<double>(rho) * kR * T * sw);
+      features(T, p, lndt, y, x);
+#pragma unroll
+      for (int j = 0; j < kNIn; ++j) {   // the box with a margin of 1e-3 of each range (rounding)
+        const float mg = 1e-3f * (nm.hi_x[j] - nm.lo_x[j]);
+        inbox = inbox && x[j] >= nm.lo_x[j] - mg && x[j] <= nm.hi_x[j] + mg;
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < kNS; ++k) y[k] = 0.0f;
+#pragma unroll
+      for (int j = 0; j < kNIn; ++j) x[j] = nm.mu_x[j];
+    }
+    // standardised features -> BF16 row t of the X tile
+    {
+      uint32_t w[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int c0 = 2 * j, c1 = 2 * j + 1;
+        const float v0 = c0 < kNIn ? (x[c0] - nm.mu_x[c0]) / nm.sd_x[c0] : 0.0f;
+        const float v1 = c1 < kNIn ? (x[c1] - nm.mu_x[c1]) / nm.sd_x[c1] : 0.0f;
+        const __nv_bfloat162 b2 = __floats2bfloat162_rn(v0, v1);
+        w[j] = *reinterpret_cast<const uint32_t*>(&b2);
+      }
+      *reinterpret_cast<uint4*>(sX + tc::kmajor_offset(t, 0, kKIn)) = make_uint4(w[0], w[1], w[2], w[3]);
+      *reinterpret_cast<uint4*>(sX + tc::kmajor_offset(t, 8, kKIn)) = make_uint4(w[4], w[5], w[6], w[7]);
+    }
+    float o[kNOutPad];
+#pragma unroll 1
+    for (int layer = 0; layer < 5; ++layer) {
+      tc::fence_async_smem();
+      tc::fence_before_sync();
+      __syncthreads();
+      if (t == 0) {
+        tc::fence_after_sync();
+        const int K = layer == 0 ? kKIn : kH;
+        const int N = layer == 4 ? kNOutPad : kH;
+        const unsigned char* Asm = layer == 0 ? sX : sHt;
+        const int wb = layer == 0 ? bW1 : (layer == 1 ? bW2 : (layer == 2 ? bW3 : (layer == 3 ? bW4 : bW5)));
+        const uint32_t idesc = tc::idesc_bf16_f32(kH, N);
+        for (int kk = 0; kk < K / 16; ++kk) {
+          const uint64_t ad = tc::smem_desc(tc::smem_u32(Asm) + kk * 256, 128, (K / 8) * 128);
+          const uint64_t bd = tc::smem_desc(tc::smem_u32(sS + wb) + kk * 256, 128, (K / 8) * 128);
+          tc::mma_bf16(taddr, ad, bd, idesc, kk > 0);
+        }
+        tc::mma_commit(&bar_mma);
+      }
+      ok = ok && tc::mbar_wait(&bar_mma, phase);
+      phase ^= 1u;
+      ok = __syncthreads_and(ok);
+      if (!ok) break;
+      tc::fence_after_sync();
+      if (layer < 4) {
+        const float* bl = bias + layer * kH;
+        for (int n0 = 0; n0 < kH; n0 += 16) {
+          float v[16];
+          tc::tmem_ld16(lane_addr + n0, v);
+          uint32_t w[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const __nv_bfloat162 b2 =
+                __floats2bfloat162_rn(gelu(v[2 * j] + bl[n0 + 2 * j]), gelu(v[2 * j + 1] + bl[n0 + 2 * j + 1]));
+            w[j] = *reinterpret_cast<const uint32_t*>(&b2);
+          }
+          *reinterpret_cast<uint4*>(sHt + tc::kmajor_offset(t, n0, kH)) = make_uint4(w[0], w[1], w[2], w[3]);
+          *reinterpret_cast<uint4*>(sHt + tc::kmajor_offset(t, n0 + 8, kH)) = make_uint4(w[4], w[5], w[6], w[7]);
+        }
+      } else {
+        tc::tmem_ld16(lane_addr, o);
+#pragma unroll
+        for (int j = 0; j < kNOutPad; ++j) o[j] += bias[4 * kH + j];
+      }
+    }
+    if (!ok) break;
+    if (valid) {
+      if (a.out) {
+#pragma unroll
+        for (int j = 0; j < kNOut; ++j) a.out[i * kNOut + j] = o[j];
+      }
+      bool acc = inbox && (o[kNS + 1] <= a.gate_log10);
+      if (acc) {
+        float yn[kNS], T1;
+        decode_state(nm, o, y, T, yn, &T1);
+        double sdy = 0.0;
+#pragma unroll
+        for (int k = 0; k < kNS; ++k) {
+          sdy += static_cast<double>(yn[k]) - static_cast<double>(y[k]);
+          acc = acc && isfinite(yn[k]) && yn[k] >= -a.atol && yn[k] <= 1.0f + 1e-6f;
+        }
+        acc = acc && fabs(sdy) <= 1e-7;
+        if (acc) {
+          bool okT;
+          const double Tg = T1;
+          const double Tn = temperature_from_energy<kNS>(m, yn, static_cast<double>(e), Tg, &okT);
+          acc = okT && fabs(Tn - Tg) <= 1e-4 * Tn;
+          if (acc) {
+            double sw = 0.0;
+#pragma unroll
+            for (int k = 0; k < kNS; ++k) {
+              a.Y[k * a.ld + i] = yn[k];
+              sw += static_cast<double>(yn[k]) * m.e64[k * 8 + 6];
+            }
+            a.T[i] = static_cast<float>(Tn);
+            if (a.p) a.p[i] = static_cast<float>(static_cast<double>(rho) * kR * Tn * sw);
+            if (a.substeps) a.substeps[i] = 0;
+            ++c_acc;
+          }
+        }
+      }
+      if (a.accepted) a.accepted[i] = acc ? 1 : 0;
+    }
+  }
+  if (!ok) {
+    // an MMA did not signal completion in time: record it and give it a second bounded chance
+    // to finish before the accumulator is freed (phase was flipped past the missed completion)
+    if (t == 0) atomicOr(a.status, 32);
+    tc::mbar_wait(&bar_mma, phase ^ 1u);
+  }
+  // every thread waited for the last commit of the tiles it ran; free the accumulator
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(taddr, 128);
+  for (int off = 16; off > 0; off >>= 1) c_acc += __shfl_down_sync(0xffffffffu, c_acc, off);
+  if (lane == 0 && c_acc) atomicAdd(a.n_accepted, c_acc);
+}
+
+size_t infer_smem_bytes(unsigned mech_bytes) {
+  return ((kBlobBytes + 1023) & ~1023) + ((mech_bytes + 1023) & ~1023) + kH * kKIn * 2 + kH * kH * 2;
+}
+
+// ====================================================================== host side
+
+struct State {
+  float* params = nullptr;   // [kNParams] FP32 masters
+  float* grads = nullptr;
+  float* m = nullptr;
+  float* v = nullptr;
+  Norm* norm = nullptr;      // device
+  Norm hnorm{};              // host copy
+  unsigned char* blob = nullptr;
+  bool blob_dirty = true;
+  unsigned long long* n_acc = nullptr;
+  int* status = nullptr;
+  float* loss = nullptr;
+  long long adam_t = 0;
+  // batch scratch, sized for `cap` samples
+  int cap = 0;
+  float *Xn = nullptr, *Tn = nullptr, *Raw = nullptr, *Z[5] = {}, *A[4] = {}, *dZ = nullptr, *dA = nullptr;
+  int* idx = nullptr;
+  long long idx_cap = 0;
+};
+
+void free_batch(State* s) {
+  cudaFree(s->Xn);
+  cudaFree(s->Tn);
+  cudaFree(s->Raw);
+  for (auto& z : s->Z) cudaFree(z);
+  for (auto& a : s->A) cudaFree(a);
+  cudaFree(s->dZ);
+  cudaFree(s->dA);
+  s->Xn = s->Tn = s->Raw = s->dZ = s->dA = nullptr;
+  for (auto& z : s->Z) z = nullptr;
+  for (auto& a : s->A) a = nullptr;
+  s->cap = 0;
+}
+
+void free_state(State* s) {
+  if (!s) return;
+  cudaFree(s->params);
+  cudaFree(s->grads);
+  cudaFree(s->m);
+  cudaFree(s->v);
+  cudaFree(s->norm);
+  cudaFree(s->blob);
+  cudaFree(s->n_acc);
+  cudaFree(s->status);
+  cudaFree(s->loss);
+  cudaFree(s->idx);
+  free_batch(s);
+  delete s;
+}
+
+int ensure_batch(State* s, int B) {
+  if (s->cap >= B) return CHEM_OK;
+  free_batch(s);
+  const size_t b = static_cast<size_t>(B);
+  bool ok = cudaMalloc(&s->Xn, sizeof(float) * b * kKIn) == cudaSuccess &&
+            cudaMalloc(&s->Tn, sizeof(float) * b * kNTgt) == cudaSuccess &&
+            cudaMalloc(&s->Raw, sizeof(float) * b * kRaw) == cudaSuccess &&
+            cudaMalloc(&s->dZ, sizeof(float) * b * kH) == cudaSuccess &&
+            cudaMalloc(&s->dA, sizeof(float) * b * kH) == cudaSuccess;
+  for (int l = 0; l < 5 && ok; ++l) ok = cudaMalloc(&s->Z[l], sizeof(float) * b * (l < 4 ? kH : kNOut)) == cudaSuccess;
+  for (int l = 0; l < 4 && ok; ++l) ok = cudaMalloc(&s->A[l], sizeof(float) * b * kH) == cudaSuccess;
+  if (!ok) {
+    free_batch(s);
+    return CHEM_ENOMEM;
+  }
+  s->cap = B;
+  return CHEM_OK;
+}
+
+int ensure_idx(State* s, long long n) {
+  if (s->idx_cap >= n) return CHEM_OK;
+  cudaFree(s->idx);
+  s->idx = nullptr;
+  s->idx_cap = 0;
+  if (cudaMalloc(&s->idx, sizeof(int) * static_cast<size_t>(n)) != cudaSuccess) return CHEM_ENOMEM;
+  s->idx_cap = n;
+  return CHEM_OK;
+}
+
+GemmArgs gemm(const float* A, long long sam, long long sak, const float* B, long long sbn, long long sbk, float* C,
+              long long ldc, int M, int N, int K, int epi, const float* bias, float* C2, int* status) {
+  GemmArgs g{};
+  g.A = A;
+  g.sam = sam;
+  g.sak = sak;
+  g.B = B;
+  g.sbn = sbn;
+  g.sbk = sbk;
+  g.C = C;
+  g.ldc = ldc;
+  g.C2 = C2;
+  g.bias = bias;
+  g.M = M;
+  g.N = N;
+  g.K = K;
+  g.epi = epi;
+  g.status = status;
+  return g;
+}
+
+constexpr int kWo[5] = {oW1, oW2, oW3, oW4, oW5};
+constexpr int kBo[5] = {oB1, oB2, oB3, oB4, oB5};
+constexpr int kIn[5] = {kNIn, kH, kH, kH, kH};
+constexpr int kOut[5] = {kH, kH, kH, kH, kNOut};
+constexpr int kEpiStore = 0, kEpiBias = 1, kEpiBiasGelu = 2, kEpiAtomic = 3;   // as in mlp.cu
+
+// forward of a batch of B standardised rows Xn [B][16] through the GEMM kernels: Z_l (pre-
+// activation) and A_l = gelu(Z_l) for the hidden layers, Z_5 = the outputs
+int forward(State* s, int B, cudaStream_t st) {
+  int r = 0;
+  for (int l = 0; l < 5 && !r; ++l) {
+    const float* in = l == 0 ? s->Xn : s->A[l - 1];
+    const long long ldin = l == 0 ? kKIn : kH;
+    r = launch_gemm(gemm(in, ldin, 1, s->params + kWo[l], kIn[l], 1, s->Z[l], kOut[l], B, kOut[l], kIn[l],
+                         l < 4 ? kEpiBiasGelu : kEpiBias, s->params + kBo[l], l < 4 ? s->A[l] : nullptr, s->status),
+                    1, st);
+  }
+  return r;
+}
+
+// loss gradient of the batch into s->grads (zeroed here); the batch loss is added to s->loss
+int backward(State* s, int B, float err_weight, cudaStream_t st) {
+  int r = 0;
+  cudaMemsetAsync(s->grads, 0, sizeof(float) * kNParams, st);
+  loss_kernel<<<(B + 255) / 256, 256, 0, st>>>(s->Z[4], s->Tn, s->Raw, B, s->norm, err_weight, s->dZ, s->loss);
+  const int ks = B >= 2048 ? 16 : (B >= 512 ? 4 : 1);   // batch split of the weight gradients
+  for (int l = 4; l >= 0 && !r; --l) {
+    const int nin = kIn[l], nout = kOut[l];
+    const float* inact = l == 0 ? s->Xn : s->A[l - 1];
+    const long long ldin = l == 0 ? kKIn : kH;
+    // dW[out][in] = sum_b dZ[b][out] in[b][in]
+    r = launch_gemm(gemm(s->dZ, 1, nout, inact, 1, ldin, s->grads + kWo[l], nin, nout, nin, B, kEpiAtomic, nullptr,
+                         nullptr, s->status),
+                    ks, st);
+    if (r) break;
+    bias_grad_kernel<<<64, 128, 0, st>>>(s->dZ, B, nout, s->grads + kBo[l]);
+    if (l == 0) break;
+    // dA[b][in] = sum_out dZ[b][out] W[out][in], then dZ_{l-1} = dA * gelu'(Z_{l-1})
+    r = launch_gemm(gemm(s->dZ, nout, 1, s->params + kWo[l], 1, nin, s->dA, nin, B, nin, nout, kEpiStore, nullptr,
+                         nullptr, s->status),
+                    1, st);
+    if (r) break;
+    const long long ne = static_cast<long long>(B) * kH;
+    gelu_back_kernel<<<static_cast<int>((ne + 255) / 256), 256, 0, st>>>(s->dA, s->Z[l - 1], s->dZ, ne);
+  }
+  return r ? r : static_cast<int>(cudaGetLastError());
+}
+
+float decode_key(unsigned int key) {
+  const unsigned int b = (key & 0x80000000u) ? (key & 0x7FFFFFFFu) : ~key;
+  float f;
+  std::memcpy(&f, &b, 4);
+  return f;
+}
+
+}  // namespace sg
+
+// accessors of the context (abi.cu)
+sg::State* ctx_surrogate(chem_ctx* c);
+void ctx_set_surrogate(chem_ctx* c, sg::State* s);
+void ctx_mech_host(const chem_ctx* c, int* ns, int* nr, const double** W, const int8_t** nuf, const int8_t** nur);
+const unsigned char* ctx_blob(const chem_ctx* c, unsigned* bytes);
+int ctx_advance_skip(chem_ctx* c, float* T, float* p, float* Y, int64_t ld, const float* rho, const float* e, int64_t n,
+                     double dt, int32_t* substeps, const unsigned char* skip, cudaStream_t st);
+void surrogate_release(sg::State* s) { sg::free_state(s); }
+
+}  // namespace chem
+
+using namespace chem;
+using namespace chem::sg;
+
+namespace {
+
+// Orthonormal basis of the complement of span{W .* (nu_r - nu_f)_r}: the directions of Y that no
+// reaction changes (element and total-mass conservation).  Returns the number of directions.
+int conserved_directions(int ns, int nr, const double* W, const int8_t* nuf, const int8_t* nur,
+                         float C[kMaxCons][kNS]) {
+  std::vector<std::vector<double>> Q;
+  auto orth = [&](std::vector<double>& v) {
+    for (int pass = 0; pass < 2; ++pass)
+      for (const auto& q : Q) {
+        double d = 0.0;
+        for (int k = 0; k < ns; ++k) d += q[k] * v[k];
+        for (int k = 0; k < ns; ++k) v[k] -= d * q[k];
+      }
+    double nrm = 0.0;
+    for (double x : v) nrm += x * x;
+    return std::sqrt(nrm);
+  };
+  for (int r = 0; r < nr; ++r) {
+    std::vector<double> v(ns);
+    double n0 = 0.0;
+    for (int k = 0; k < ns; ++k) {
+      v[k] = W[k] * (nur[r * ns + k] - nuf[r * ns + k]);
+      n0 += v[k] * v[k];
+    }
+    const double nrm = orth(v);
+    if (nrm > 1e-9 * std::sqrt(n0) && nrm > 0.0) {
+      for (double& x : v) x /= nrm;
+      Q.push_back(v);
+    }
+  }
+  const size_t nreact = Q.size();
+  int m = 0;
+  for (int j = 0; j < ns; ++j) {
+    std::vector<double> v(ns, 0.0);
+    v[j] = 1.0;
+    const double nrm = orth(v);
+    if (nrm > 1e-6) {
+      for (double& x : v) x /= nrm;
+      Q.push_back(v);
+      if (m < kMaxCons)
+        for (int k = 0; k < ns; ++k) C[m][k] = static_cast<float>(v[k]);
+      ++m;
+    }
+  }
+  (void)nreact;
+  return m;
+}
+
+int fail_cuda(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return CHEM_OK;
+  std::fprintf(stderr, "libchem (surrogate): %s: %s\n", what, cudaGetErrorString(e));
+  return CHEM_ECUDA;
+}
+
+State* get_state(chem_ctx* ctx) { return ctx ? ctx_surrogate(ctx) : nullptr; }
+
+int upload_norm(State* s, cudaStream_t st) {
+  s->blob_dirty = true;
+  int rc = fail_cuda(cudaMemcpyAsync(s->norm, &s->hnorm, sizeof(Norm), cudaMemcpyHostToDevice, st), "norm");
+  return rc ? rc : fail_cuda(cudaStreamSynchronize(st), "norm");
+}
+
+int device_status(State* s, cudaStream_t st) {
+  int h = 0;
+  cudaMemcpyAsync(&h, s->status, sizeof(int), cudaMemcpyDeviceToHost, st);
+  const int rc = fail_cuda(cudaStreamSynchronize(st), "status");
+  if (rc) return rc;
+  if (h) {
+    std::fprintf(stderr, "libchem (surrogate): device status %#x (tensor-core wait timed out)\n", h);
+    return CHEM_ECUDA;
+  }
+  return CHEM_OK;
+}
+
+int launch_infer(chem_ctx* ctx, State* s, const GatedArgs& g0, cudaStream_t st) {
+  if (s->blob_dirty) {
+    pack_blob_kernel<<<64, 256, 0, st>>>(s->params, s->norm, s->blob);
+    s->blob_dirty = false;
+  }
+  GatedArgs g = g0;
+  g.mech = ctx_blob(ctx, &g.mech_bytes);
+  g.sblob = s->blob;
+  g.n_accepted = s->n_acc;
+  g.status = s->status;
+  const size_t smem = infer_smem_bytes(g.mech_bytes);
+  cudaFuncSetAttribute(surrogate_infer_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const long long tiles = (g.n + kH - 1) / kH;
+  const int grid = static_cast<int>(tiles < sms ? tiles : sms);
+  surrogate_infer_kernel<<<grid, 128, smem, st>>>(g);
+  return fail_cuda(cudaGetLastError(), "surrogate kernel");
+}
+
+}  // namespace
+
+extern "C" {
+
+int chem_surrogate_nparams(void) { return kNParams; }
+
+int chem_surrogate_init(chem_ctx* ctx, uint64_t seed) {
+  if (!ctx) return CHEM_EINVAL;
+  int ns, nr;
+  const double* W;
+  const int8_t *nuf, *nur;
+  ctx_mech_host(ctx, &ns, &nr, &W, &nuf, &nur);
+  if (ns != kNS) return CHEM_EUNSUPPORTED;
+  Norm nm{};
+  const int m = conserved_directions(ns, nr, W, nuf, nur, nm.C);
+  if (m > kMaxCons) return CHEM_EUNSUPPORTED;
+  State* s = get_state(ctx);
+  if (!s) {
+    s = new State();
+    bool ok = cudaMalloc(&s->params, sizeof(float) * kNParams) == cudaSuccess &&
+              cudaMalloc(&s->grads, sizeof(float) * kNParams) == cudaSuccess &&
+              cudaMalloc(&s->m, sizeof(float) * kNParams) == cudaSuccess &&
+              cudaMalloc(&s->v, sizeof(float) * kNParams) == cudaSuccess &&
+              cudaMalloc(&s->norm, sizeof(Norm)) == cudaSuccess && cudaMalloc(&s->blob, kBlobBytes) == cudaSuccess &&
+              cudaMalloc(&s->n_acc, sizeof(unsigned long long)) == cudaSuccess &&
+              cudaMalloc(&s->status, sizeof(int)) == cudaSuccess && cudaMalloc(&s->loss, sizeof(float)) == cudaSuccess;
+    if (!ok) {
+      free_state(s);
+      return CHEM_ENOMEM;
+    }
+    ctx_set_surrogate(ctx, s);
+  }
+  // He initialisation of the weights (output layer scaled down), zero biases and moments
+  std::vector<float> h(kNParams, 0.0f);
+  std::mt19937_64 rng(seed);
+  for (int l = 0; l < 5; ++l) {
+    std::normal_distribution<float> nd(0.0f, std::sqrt(2.0f / kIn[l]) * (l == 4 ? 0.5f : 1.0f));
+    for (int i = 0; i < kIn[l] * kOut[l]; ++i) h[kWo[l] + i] = nd(rng);
+  }
+  int rc = fail_cuda(cudaMemcpy(s->params, h.data(), sizeof(float) * kNParams, cudaMemcpyHostToDevice), "init");
+  if (rc) return rc;
+  cudaMemset(s->m, 0, sizeof(float) * kNParams);
+  cudaMemset(s->v, 0, sizeof(float) * kNParams);
+  cudaMemset(s->status, 0, sizeof(int));
+  s->adam_t = 0;
+  for (int j = 0; j < kNIn; ++j) nm.sd_x[j] = 1.0f;
+  for (int j = 0; j < kNTgt; ++j) nm.sd_y[j] = 1.0f;
+  for (int j = 0; j < kNIn; ++j) {   // empty box: nothing is accepted before training
+    nm.lo_x[j] = 1.0f;
+    nm.hi_x[j] = -1.0f;
+  }
+  nm.ncons = m;
+  s->hnorm = nm;
+  return upload_norm(s, nullptr);
+}
+
+int chem_surrogate_train(chem_ctx* ctx, const float* X, const float* Yt, int64_t n, const chem_train_cfg* cfg,
+                         float* loss_per_epoch, void* stream) {
+  State* s = get_state(ctx);
+  if (!s || !X || !Yt || !cfg || cfg->epochs < 0 || cfg->batch < 128 || (cfg->batch % 128) || !(cfg->lr > 0) ||
+      n < cfg->batch || n > 0x7fffffffLL || !(cfg->weight_decay >= 0) || !(cfg->err_weight >= 0))
+    return CHEM_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int B = cfg->batch;
+  int rc = ensure_batch(s, B);
+  if (!rc) rc = ensure_idx(s, n);
+  if (rc) return rc;
+  // normalisation statistics and the training box of this data set
+  constexpr int NT = kNIn + kNTgt;
+  double* acc = nullptr;
+  unsigned int* mm = nullptr;
+  if (cudaMalloc(&acc, sizeof(double) * 2 * NT) != cudaSuccess) return CHEM_ENOMEM;
+  if (cudaMalloc(&mm, sizeof(unsigned int) * 2 * kNIn) != cudaSuccess) {
+    cudaFree(acc);
+    return CHEM_ENOMEM;
+  }
+  cudaMemsetAsync(acc, 0, sizeof(double) * 2 * NT, st);
+  unsigned int init[2 * kNIn];
+  for (int j = 0; j < kNIn; ++j) {
+    init[j] = 0xFFFFFFFFu;
+    init[kNIn + j] = 0u;
+  }
+  cudaMemcpyAsync(mm, init, sizeof(init), cudaMemcpyHostToDevice, st);
+  stats_kernel<<<304, 128, 0, st>>>(X, Yt, n, acc, mm);
+  double hacc[2 * NT];
+  unsigned int hmm[2 * kNIn];
+  cudaMemcpyAsync(hacc, acc, sizeof(hacc), cudaMemcpyDeviceToHost, st);
+  cudaMemcpyAsync(hmm, mm, sizeof(hmm), cudaMemcpyDeviceToHost, st);
+  rc = fail_cuda(cudaStreamSynchronize(st), "statistics");
+  cudaFree(acc);
+  cudaFree(mm);
+  if (rc) return rc;
+  Norm& nm = s->hnorm;
+  for (int j = 0; j < NT; ++j) {
+    const double mu = hacc[j] / static_cast<double>(n);
+    const double var = std::fmax(hacc[NT + j] / static_cast<double>(n) - mu * mu, 0.0);
+    const float sd = static_cast<float>(std::sqrt(var) > 1e-12 ? std::sqrt(var) : 1.0);
+    if (!std::isfinite(mu) || !std::isfinite(var)) return CHEM_EINVAL;   // non-finite samples
+    if (j < kNIn) {
+      nm.mu_x[j] = static_cast<float>(mu);
+      nm.sd_x[j] = sd;
+    } else {
+      nm.mu_y[j - kNIn] = static_cast<float>(mu);
+      nm.sd_y[j - kNIn] = sd;
+    }
+  }
+  for (int j = 0; j < kNIn; ++j) {
+    nm.lo_x[j] = decode_key(hmm[j]);
+    nm.hi_x[j] = decode_key(hmm[kNIn + j]);
+  }
+  if ((rc = upload_norm(s, st))) return rc;
+  // epochs of shuffled mini-batches (full batches only)
+  std::vector<int> order(static_cast<size_t>(n));
+  for (int64_t i = 0; i < n; ++i) order[i] = static_cast<int>(i);
+  std::mt19937_64 rng(cfg->seed ^ 0x9E3779B97F4A7C15ull);
+  const int64_t nb = n / B;
+  const int64_t total_steps = nb * cfg->epochs;
+  int64_t step = 0;
+  for (int ep = 0; ep < cfg->epochs; ++ep) {
+    std::shuffle(order.begin(), order.end(), rng);
+    cudaMemcpyAsync(s->idx, order.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st);
+    cudaMemsetAsync(s->loss, 0, sizeof(float), st);
+    for (int64_t bi = 0; bi < nb; ++bi, ++step) {
+      batch_kernel<<<(B + 127) / 128, 128, 0, st>>>(X, Yt, s->idx + bi * B, B, s->norm, s->Xn, s->Tn, s->Raw);
+      if ((rc = forward(s, B, st))) return fail_cuda(static_cast<cudaError_t>(rc), "forward");
+      if ((rc = backward(s, B, cfg->err_weight, st))) return fail_cuda(static_cast<cudaError_t>(rc), "backward");
+      const double lr = 0.5 * cfg->lr * (1.0 + std::cos(3.14159265358979 * static_cast<double>(step) /
+                                                          static_cast<double>(total_steps)));
+      ++s->adam_t;
+      const float c1 = static_cast<float>(1.0 - std::pow(0.9, static_cast<double>(s->adam_t)));
+      const float c2 = static_cast<float>(1.0 - std::pow(0.999, static_cast<double>(s->adam_t)));
+      adamw_kernel<<<(kNParams + 255) / 256, 256, 0, st>>>(s->params, s->grads, s->m, s->v, kNParams,
+                                                           static_cast<float>(lr), 0.9f, 0.999f, 1e-8f,
+                                                           static_cast<float>(cfg->weight_decay), c1, c2);
+    }
+    float l = 0.0f;
+    cudaMemcpyAsync(&l, s->loss, sizeof(float), cudaMemcpyDeviceToHost, st);
+    if ((rc = fail_cuda(cudaStreamSynchronize(st), "epoch"))) return rc;
+    if (loss_per_epoch) loss_per_epoch[ep] = l / static_cast<float>(nb);
+  }
+  s->blob_dirty = true;
+  return device_status(s, st);
+}
+
+int chem_surrogate_grads(chem_ctx* ctx, const float* X, const float* Yt, int32_t n, float err_weight, float* grads,
+                         float* loss, void* stream) {
+  State* s = get_state(ctx);
+  if (!s || !X || !Yt || n < 128 || (n % 128) || !grads || !loss || !(err_weight >= 0)) return CHEM_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int rc = ensure_batch(s, n);
+  if (rc) return rc;
+  cudaMemsetAsync(s->loss, 0, sizeof(float), st);
+  batch_kernel<<<(n + 127) / 128, 128, 0, st>>>(X, Yt, nullptr, n, s->norm, s->Xn, s->Tn, s->Raw);
+  if ((rc = forward(s, n, st))) return fail_cuda(static_cast<cudaError_t>(rc), "forward");
+  if ((rc = backward(s, n, err_weight, st))) return fail_cuda(static_cast<cudaError_t>(rc), "backward");
+  cudaMemcpyAsync(grads, s->grads, sizeof(float) * kNParams, cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(loss, s->loss, sizeof(float), cudaMemcpyDeviceToDevice, st);
+  return device_status(s, st);
+}
+
+int chem_surrogate_forward(chem_ctx* ctx, const float* X, int32_t n, float* out, void* stream) {
+  State* s = get_state(ctx);
+  if (!s || !X || n < 1 || !out) return CHEM_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  constexpr int Bmax = 8192;
+  int rc = ensure_batch(s, n < Bmax ? (n + 127) / 128 * 128 : Bmax);
+  if (rc) return rc;
+  for (int b0 = 0; b0 < n; b0 += Bmax) {
+    const int B = n - b0 < Bmax ? n - b0 : Bmax;
+    batch_kernel<<<(B + 127) / 128, 128, 0, st>>>(X + static_cast<int64_t>(b0) * kNIn, nullptr, nullptr, B, s->norm,
+                                                  s->Xn, nullptr, nullptr);
+    if ((rc = forward(s, B, st))) return fail_cuda(static_cast<cudaError_t>(rc), "forward");
+    cudaMemcpyAsync(out + static_cast<int64_t>(b0) * kNOut, s->Z[4], sizeof(float) * B * kNOut,
+                    cudaMemcpyDeviceToDevice, st);
+  }
+  return device_status(s, st);
+}
+
+int chem_surrogate_params(chem_ctx* ctx, float* dst, const float* src, void* stream) {
+  State* s = get_state(ctx);
+  if (!s || (!dst && !src)) return CHEM_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (dst) cudaMemcpyAsync(dst, s->params, sizeof(float) * kNParams, cudaMemcpyDefault, st);
+  if (src) {
+    cudaMemcpyAsync(s->params, src, sizeof(float) * kNParams, cudaMemcpyDefault, st);
+    s->blob_dirty = true;
+  }
+  return fail_cuda(cudaStreamSynchronize(st), "params");
+}
+
+int chem_surrogate_save(chem_ctx* ctx, void* buf, size_t cap, size_t* size) {
+  State* s = get_state(ctx);
+  if (!s || !size) return CHEM_EINVAL;
+  const size_t need = 16 + sizeof(Norm) + sizeof(float) * kNParams;
+  *size = need;
+  if (!buf) return CHEM_OK;
+  if (cap < need) return CHEM_EINVAL;
+  unsigned char* b = static_cast<unsigned char*>(buf);
+  const int32_t hdr[4] = {0x47534843 /* "CHSG" */, 1, kNS, kNParams};
+  std::memcpy(b, hdr, 16);
+  std::memcpy(b + 16, &s->hnorm, sizeof(Norm));
+  return fail_cuda(cudaMemcpy(b + 16 + sizeof(Norm), s->params, sizeof(float) * kNParams, cudaMemcpyDeviceToHost),
+                   "save");
+}
+
+int chem_surrogate_load(chem_ctx* ctx, const void* buf, size_t size) {
+  if (!ctx || !buf) return CHEM_EINVAL;
+  const size_t need = 16 + sizeof(Norm) + sizeof(float) * kNParams;
+  if (size != need) return CHEM_EINVAL;
+  const unsigned char* b = static_cast<const unsigned char*>(buf);
+  int32_t hdr[4];
+  std::memcpy(hdr, b, 16);
+  if (hdr[0] != 0x47534843 || hdr[1] != 1 || hdr[2] != kNS || hdr[3] != kNParams) return CHEM_EINVAL;
+  int rc = CHEM_OK;
+  if (!get_state(ctx) && (rc = chem_surrogate_init(ctx, 0))) return rc;
+  State* s = get_state(ctx);
+  Norm nm;
+  std::memcpy(&nm, b + 16, sizeof(Norm));
+  if (nm.ncons != s->hnorm.ncons) return CHEM_EINVAL;   // saved for another mechanism
+  s->hnorm = nm;
+  rc = fail_cuda(cudaMemcpy(s->params, b + 16 + sizeof(Norm), sizeof(float) * kNParams, cudaMemcpyHostToDevice),
+                 "load");
+  return rc ? rc : upload_norm(s, nullptr);
+}
+
+int chem_advance_gated(chem_ctx* ctx, float* T, float* p, float* Y, int64_t ld, const float* rho, const float* e,
+                       int64_t n, double dt, double gate_tol, uint8_t* accepted, int32_t* substeps,
+                       int64_t* n_accepted, void* stream) {
+  State* s = get_state(ctx);
+  if (!s || n < 0 || !(dt > 0) || !std::isfinite(dt) || !(gate_tol > 0) ||
+      (n > 0 && (!T || !Y || !rho || !e || !accepted || !substeps || ld < n)))
+    return CHEM_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (n_accepted) *n_accepted = 0;
+  int rc = fail_cuda(cudaMemsetAsync(s->n_acc, 0, sizeof(unsigned long long), st), "memset");
+  if (rc) return rc;
+  if (n > 0) {
+    GatedArgs g{};
+    g.T = T;
+    g.p = p;
+    g.Y = Y;
+    g.ld = ld;
+    g.rho = rho;
+    g.e = e;
+    g.n = n;
+    g.dt = dt;
+    g.gate_log10 = static_cast<float>(std::log10(gate_tol));
+    g.atol = 1e-10f;
+    g.accepted = accepted;
+    g.substeps = substeps;
+    if ((rc = launch_infer(ctx, s, g, st))) return rc;
+  }
+  // every cell the gate rejected goes through the plain bulk / stiff path
+  if ((rc = ctx_advance_skip(ctx, T, p, Y, ld, rho, e, n, dt, substeps, accepted, st))) return rc;
+  if (n_accepted) {
+    unsigned long long h = 0;
+    cudaMemcpyAsync(&h, s->n_acc, sizeof(h), cudaMemcpyDeviceToHost, st);
+    if ((rc = fail_cuda(cudaStreamSynchronize(st), "gated"))) return rc;
+    *n_accepted = static_cast<int64_t>(h);
+  }
+  return CHEM_OK;
+}
+
+int chem_surrogate_infer(chem_ctx* ctx, const float* T, const float* Y, int64_t ld, const float* rho, const float* e,
+                         int64_t n, double dt, float* out, void* stream) {
+  State* s = get_state(ctx);
+  if (!s || n < 1 || !T || !Y || !rho || !e || !out || ld < n || !(dt > 0)) return CHEM_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  GatedArgs g{};
+  g.T = const_cast<float*>(T);   // read only: with gate_log10 = -inf no cell is accepted or written
+  g.p = nullptr;
+  g.Y = const_cast<float*>(Y);
+  g.ld = ld;
+  g.rho = rho;
+  g.e = e;
+  g.n = n;
+  g.dt = dt;
+  g.gate_log10 = -INFINITY;
+  g.atol = 1e-10f;
+  g.out = out;
+  const int rc = launch_infer(ctx, s, g, st);
+  return rc ? rc : device_status(s, st);
+}
+
+}  // extern "C"

@@ -162,11 +162,19 @@ def helix_box_fields(mech, boxes, seed=0, stiff_frac=0.03, alpha=0.5):
 
 
 def surrogate_samples(mech, n, seed=0, alpha=0.5, T_range=(300.0, 3200.0), p_atm=(1.0, 50.0),
-                      log_dt=(np.log(1e-9), np.log(1e-6))):
-    """Inputs of surrogate training samples: T, p, Y ~ Dirichlet, dt log-uniform."""
+                      log_dt=(np.log(1e-9), np.log(1e-6)), premix_frac=0.0, kappa=200.0, alpha_trace=1e-3):
+    """Inputs of surrogate training samples: T, p, Y ~ Dirichlet, dt log-uniform.
+
+    A fraction `premix_frac` of the samples draws Y from a Dirichlet concentrated on the
+    stoichiometric premix (concentrations kappa * Y_premix + alpha_trace): near-premix states with
+    trace radicals, the cold part of the reacting-front fields; the rest from Dirichlet(alpha)."""
     rng = np.random.default_rng(seed + 15485863)
     T = rng.uniform(*T_range, size=n)
     p = rng.uniform(*p_atm, size=n) * P_ATM
     Y = rng.dirichlet(np.full(mech["ns"], alpha), size=n).T
     dt = np.exp(rng.uniform(*log_dt, size=n))
+    if premix_frac > 0:
+        pick = rng.random(n) < premix_frac
+        conc = kappa * premix_mass_fractions(mech) + alpha_trace
+        Y[:, pick] = rng.dirichlet(conc, size=int(pick.sum())).T
     return T, p, Y, dt

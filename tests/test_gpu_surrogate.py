@@ -1,0 +1,294 @@
+"""The learned surrogate on the GPU: gradients, statistics, fused inference, the gate, the gain.
+
+* The loss gradient of the tensor-core training path equals the FP64 oracle's reverse-mode
+  gradient (oracle/mlp.py, pinned by finite differences): tightly when the oracle rounds the
+  operands of its products to BF16 as the interface states, loosely in plain FP64.
+* The normalisation statistics and the conserved directions the library derives match the
+  oracle's (the directions from the element matrix, the library's from the reaction span).
+* The fused inference kernel equals the GEMM forward and the oracle's forward.
+* With a gate that accepts nothing the gated step is bit-identical to chem_advance.
+* A network trained on pairs from the plain integrator (a sample of them checked against the
+  oracle) accepts cells whose oracle error is within the parity bar (false-accept rate
+  measured), and the gain over the plain method is measured on a reacting-sheet field.
+"""
+import time
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle
+from oracle import mlp
+import paper_2510_23993_gb300 as chem
+from paper_2510_23993_gb300 import surrogate
+import synth
+
+DEV = "cuda:0"
+Y_BIG, TOL_Y, ABS_Y, TOL_T = 1e-6, 1e-4, 1e-10, 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    chem.build()
+
+
+def _raw_batch(mech, n, seed, premix_frac=0.5):
+    """Raw rows X = (T, p, dt, Y) and Yt = (Y1, T1) (synthetic new states), float32."""
+    T, p, Y, dt = synth.surrogate_samples(mech, n, seed=seed, premix_frac=premix_frac)
+    rng = np.random.default_rng(seed + 99)
+    Y1 = np.clip(Y * (1 + rng.normal(scale=0.02, size=Y.shape)), 0.0, 1.0)
+    T1 = T + rng.normal(scale=20.0, size=n)
+    X = np.column_stack([T, p, dt, Y.T]).astype(np.float32)
+    Yt = np.column_stack([Y1.T, T1]).astype(np.float32)
+    return X, Yt
+
+
+def _oracle_checkpoint(mech, X, Yt, seed):
+    """Normalisation from the data (oracle), conserved directions from the element matrix, seeded
+    He-initialised parameters; returns the checkpoint bytes and the stored (FP32) values."""
+    Xd, Yd = X.astype(np.float64), Yt.astype(np.float64)
+    F = mlp.features(Xd[:, 0], Xd[:, 1], Xd[:, 2], Xd[:, 3:])
+    A = mlp.targets(Xd[:, 0], Xd[:, 3:], Yd[:, :9], Yd[:, 9])
+    norm = mlp.norm_from_data(F, A)
+    C = mlp.conserved_basis(mech["elem"], mech["W"])
+    norm["C"] = np.vstack([C, np.zeros((mlp.MAX_CONS - C.shape[0], 9))])
+    norm["ncons"] = C.shape[0]
+    rng = np.random.default_rng(seed)
+    layers = []
+    for l in range(5):
+        nin, nout = mlp.WIDTHS[l], mlp.WIDTHS[l + 1]
+        layers.append((rng.normal(0, np.sqrt(2.0 / nin), (nout, nin)), rng.normal(0, 0.05, nout)))
+    params = mlp.flatten(layers).astype(np.float32)
+    blob = mlp.pack_checkpoint(norm, params)
+    return blob, mlp.unpack_checkpoint(blob)
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def _layer_slices():
+    out, off = [], 0
+    for l in range(5):
+        nin, nout = mlp.WIDTHS[l], mlp.WIDTHS[l + 1]
+        out.append((f"W{l + 1}", slice(off, off + nin * nout)))
+        off += nin * nout
+        out.append((f"b{l + 1}", slice(off, off + nout)))
+        off += nout
+    return out
+
+
+def test_gradients_match_oracle(h2mech):
+    X, Yt = _raw_batch(h2mech, 1024, seed=11)
+    blob, (norm, params) = _oracle_checkpoint(h2mech, X, Yt, seed=3)
+    ctx = chem.Context(h2mech, max_cells=1024)
+    ctx.surrogate_init(0)
+    ctx.surrogate_load(blob)
+    n = mlp.n_params()
+    assert chem.chem_surrogate_nparams() == n
+    g = torch.zeros(n, dtype=torch.float32, device=DEV)
+    loss = torch.zeros(1, dtype=torch.float32, device=DEV)
+    ctx.surrogate_grads(_dev(X), _dev(Yt), 0.1, g, loss)
+    g = g.cpu().numpy().astype(np.float64)
+    Xd, Yd = X.astype(np.float64), Yt.astype(np.float64)
+    l_emu, g_emu = mlp.surrogate_loss_and_grad(norm, params, Xd, Yd, 0.1, bf16_products=True)
+    l_ex, g_ex = mlp.surrogate_loss_and_grad(norm, params, Xd, Yd, 0.1, bf16_products=False)
+    assert abs(loss.item() - l_emu) <= 1e-4 * l_emu
+    assert abs(loss.item() - l_ex) <= 2e-2 * l_ex
+    for name, sl in _layer_slices():
+        e_emu = np.linalg.norm(g[sl] - g_emu[sl]) / np.linalg.norm(g_emu[sl])
+        e_ex = np.linalg.norm(g[sl] - g_ex[sl]) / np.linalg.norm(g_ex[sl])
+        assert e_emu <= 3e-3, (name, e_emu)
+        assert e_ex <= 5e-2, (name, e_ex)
+    ctx.close()
+
+
+def test_statistics_and_conserved_directions_match_oracle(h2mech):
+    X, Yt = _raw_batch(h2mech, 8192, seed=12)
+    ctx = chem.Context(h2mech, max_cells=16)
+    ctx.surrogate_init(0)
+    norm0, _ = mlp.unpack_checkpoint(ctx.surrogate_save())
+    C_lib = norm0["C"][:norm0["ncons"]]
+    C_or = mlp.conserved_basis(h2mech["elem"], h2mech["W"])
+    assert norm0["ncons"] == C_or.shape[0]
+    assert np.allclose(C_lib.T @ C_lib, C_or.T @ C_or, atol=1e-6)
+    losses = ctx.surrogate_train(_dev(X), _dev(Yt), epochs=0)
+    assert losses == []
+    norm, _ = mlp.unpack_checkpoint(ctx.surrogate_save())
+    Xd, Yd = X.astype(np.float64), Yt.astype(np.float64)
+    F = mlp.features(Xd[:, 0], Xd[:, 1], Xd[:, 2], Xd[:, 3:])
+    A = mlp.targets(Xd[:, 0], Xd[:, 3:], Yd[:, :9], Yd[:, 9])
+    ref = mlp.norm_from_data(F, A)
+    assert np.all(np.abs(norm["mu_x"] - ref["mu_x"]) <= 1e-4 * ref["sd_x"])
+    assert np.allclose(norm["sd_x"], ref["sd_x"], rtol=1e-4)
+    assert np.all(np.abs(norm["mu_y"] - ref["mu_y"]) <= 1e-4 * ref["sd_y"])
+    assert np.allclose(norm["sd_y"], ref["sd_y"], rtol=1e-4)
+    span = ref["hi_x"] - ref["lo_x"]
+    assert np.all(np.abs(norm["lo_x"] - ref["lo_x"]) <= 1e-5 * np.maximum(span, np.abs(ref["lo_x"])))
+    assert np.all(np.abs(norm["hi_x"] - ref["hi_x"]) <= 1e-5 * np.maximum(span, np.abs(ref["hi_x"])))
+    ctx.close()
+
+
+def test_fused_inference_matches_gemm_and_oracle(h2mech):
+    n = 1000   # 7 full tiles of 128 cells and a ragged tail
+    T, p, Y, _ = synth.surrogate_samples(h2mech, n, seed=13, premix_frac=0.5)
+    dt = 3e-8
+    T32, p32, Y32 = T.astype(np.float32), p.astype(np.float32), np.ascontiguousarray(Y, dtype=np.float32)
+    rho, e = oracle.state_from_TpY(h2mech, T32, p32, Y32)
+    X = np.column_stack([T32, p32, np.full(n, dt, np.float32), Y32.T]).astype(np.float32)
+    Xn, Ytn = _raw_batch(h2mech, 4096, seed=14)
+    blob, (norm, params) = _oracle_checkpoint(h2mech, Xn, Ytn, seed=4)
+    ctx = chem.Context(h2mech, max_cells=n)
+    ctx.surrogate_load(blob)   # creates the surrogate on first use
+    o_fused = torch.zeros((n, 11), dtype=torch.float32, device=DEV)
+    ctx.surrogate_infer(_dev(T32), _dev(Y32), _dev(rho.astype(np.float32)), _dev(e.astype(np.float32)), dt, o_fused)
+    o_gemm = torch.zeros((n, 11), dtype=torch.float32, device=DEV)
+    ctx.surrogate_forward(_dev(X), o_gemm)
+    o_fused, o_gemm = o_fused.cpu().numpy().astype(np.float64), o_gemm.cpu().numpy().astype(np.float64)
+    o_emu = mlp.surrogate_outputs(norm, params, X.astype(np.float64), bf16_products=True)
+    o_ex = mlp.surrogate_outputs(norm, params, X.astype(np.float64), bf16_products=False)
+    rms = np.sqrt(np.mean(o_ex ** 2, axis=0))
+
+    def close(a, b, q99, worst):
+        # a rounding flip of one BF16 operand moves a row by up to ~1% of the output scale, so
+        # the bound is on the 99th percentile of the rows and, looser, on the worst row
+        d = np.max(np.abs(a - b) / rms, axis=1)
+        return np.percentile(d, 99) <= q99 and d.max() <= worst, (np.percentile(d, 99), d.max())
+
+    ok, info = close(o_fused, o_gemm, 1e-3, 2e-2)
+    assert ok, ("fused vs GEMM", info)
+    ok, info = close(o_gemm, o_emu, 1e-3, 2e-2)
+    assert ok, ("GEMM vs BF16-emulating oracle", info)
+    ok, info = close(o_fused, o_ex, 5e-2, 0.15)
+    assert ok, ("fused vs FP64 oracle", info)
+    ctx.close()
+
+
+def _sheet(mech, n_edge, seed):
+    T, p, Y, hot = synth.sheet_field(mech, n=n_edge, seed=seed)
+    T, p, Y = T.astype(np.float32), p.astype(np.float32), np.ascontiguousarray(Y, dtype=np.float32)
+    rho, e = oracle.state_from_TpY(mech, T, p, Y)
+    return T, p, Y, rho.astype(np.float32), e.astype(np.float32), hot
+
+
+def test_gate_closed_equals_plain(h2mech):
+    X, Yt = _raw_batch(h2mech, 4096, seed=15)
+    blob, _ = _oracle_checkpoint(h2mech, X, Yt, seed=5)
+    T, p, Y, rho, e, _ = _sheet(h2mech, 24, seed=3)
+    n = T.size
+    ctx = chem.Context(h2mech, max_cells=n)
+    ctx.surrogate_load(blob)
+    a = [_dev(v) for v in (T, p, Y)]
+    sub_a = torch.zeros(n, dtype=torch.int32, device=DEV)
+    acc = torch.full((n,), 7, dtype=torch.uint8, device=DEV)
+    na = ctx.advance_gated(a[0], a[1], a[2], _dev(rho), _dev(e), 1e-8, 1e-30, acc, sub_a)
+    st_g = ctx.status()
+    b = [_dev(v) for v in (T, p, Y)]
+    sub_b = torch.zeros(n, dtype=torch.int32, device=DEV)
+    ctx.advance(b[0], b[1], b[2], _dev(rho), _dev(e), 1e-8, sub_b)
+    st_p = ctx.status()
+    assert na == 0 and int(acc.sum()) == 0
+    assert all(torch.equal(x, y) for x, y in zip(a, b)) and torch.equal(sub_a, sub_b)
+    assert st_g["nqueued"] == st_p["nqueued"] and st_g["nbulk"] == st_p["nbulk"]
+    ctx.close()
+
+
+def _errors(mech, rho, e, T0, Y0, dt, T, Y):
+    """Per-cell parity check against the oracle, with the conditioning allowance of the plain
+    FP32 path (3x the oracle's response to a one-ulp change of e); returns (bad, eT, eY_rel)."""
+    T_ref, _, Y_ref, _ = oracle.advance(mech, rho, e, T0, Y0, dt)
+    T_p, _, Y_p, _ = oracle.advance(mech, rho, e.astype(np.float64) * (1 + 2.0 ** -23), T0, Y0, dt)
+    big = Y_ref >= Y_BIG
+    cT = np.abs(T_p - T_ref) / T_ref
+    cY = np.where(big, np.abs(Y_p - Y_ref) / np.maximum(Y_ref, 1e-300), np.abs(Y_p - Y_ref))
+    eT = np.abs(T.astype(np.float64) - T_ref) / T_ref
+    eY = np.where(big, np.abs(Y.astype(np.float64) - Y_ref) / np.maximum(Y_ref, 1e-300),
+                  np.abs(Y.astype(np.float64) - Y_ref))
+    bad = (eT > TOL_T + 3 * cT) | np.any(eY > np.where(big, TOL_Y, ABS_Y) + 3 * cY, axis=0)
+    return bad, eT, np.where(big, eY, 0.0).max(0)
+
+
+def test_trained_gate_accuracy_and_gain(h2mech):
+    """Train on 262,144 integrator-made pairs, then one gated step of a 64^3 reacting sheet."""
+    nbox, m = 256, 1024
+    n_train = nbox * m
+    Ts, ps, Ys, dts = synth.surrogate_samples(h2mech, n_train, seed=21, premix_frac=0.5)
+    ctx = chem.Context(h2mech, max_cells=max(n_train, 64 ** 3))
+    Td, pd, Yd = _dev(Ts.astype(np.float32)), _dev(ps.astype(np.float32)), _dev(Ys.astype(np.float32))
+    t0 = time.perf_counter()
+    X, Yt, keep = surrogate.make_pairs(ctx, Td, pd, Yd, dts[:nbox])
+    torch.cuda.synchronize()
+    t_pairs = time.perf_counter() - t0
+    st_pairs = ctx.status()
+    kept = keep.float().mean().item()
+    print(f"\npairs: {t_pairs:.1f} s, kept {kept:.4f}, status {st_pairs}")
+    assert kept > 0.95
+    # a sample of the training pairs against the oracle
+    rng = np.random.default_rng(0)
+    idx = rng.choice(X.shape[0], 24, replace=False)
+    Xs, Ys_ = X[idx].cpu().numpy().astype(np.float64), Yt[idx].cpu().numpy().astype(np.float64)
+    fails = []
+    for r in range(len(idx)):
+        T0, p0, dt, Y0 = Xs[r, 0], Xs[r, 1], Xs[r, 2], Xs[r, 3:]
+        rho, e = oracle.state_from_TpY(h2mech, np.float32([T0]), np.float32([p0]), Y0.astype(np.float32)[:, None])
+        rho, e = rho.astype(np.float32), e.astype(np.float32)
+        bad, eT, eY = _errors(h2mech, rho, e, np.array([T0]), Y0[:, None], dt, np.array([Ys_[r, 9]]),
+                              Ys_[r, :9][:, None])
+        if bad.any():
+            fails.append((r, T0, p0, dt, float(eT[0]), float(eY[0])))
+    assert not fails, fails
+    ctx.surrogate_init(1)
+    t0 = time.perf_counter()
+    losses = ctx.surrogate_train(X, Yt, epochs=40, batch=4096, lr=1e-3, err_weight=0.1, seed=1)
+    t_train = time.perf_counter() - t0
+    assert losses[-1] < 0.2 * losses[0], losses
+    # one gated step of a reacting sheet against the plain step
+    T, p, Y, rho, e, hot = _sheet(h2mech, 64, seed=5)
+    n = T.size
+    dt = 1e-8
+    rho_d, e_d = _dev(rho), _dev(e)
+    res = {}
+    for mode in ("plain", "gated", "plain", "gated"):   # second round is timed warm
+        s = [_dev(v) for v in (T, p, Y)]
+        sub = torch.zeros(n, dtype=torch.int32, device=DEV)
+        acc = torch.zeros(n, dtype=torch.uint8, device=DEV)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        if mode == "plain":
+            ctx.advance(s[0], s[1], s[2], rho_d, e_d, dt, sub)
+            na = 0
+        else:
+            na = ctx.advance_gated(s[0], s[1], s[2], rho_d, e_d, dt, 1e-5, acc, sub)
+        torch.cuda.synchronize()
+        res[mode] = dict(ms=1e3 * (time.perf_counter() - t0), st=ctx.status(), T=s[0].cpu().numpy(),
+                         Y=s[2].cpu().numpy(), acc=acc.cpu().numpy().astype(bool), na=na)
+    g, pl = res["gated"], res["plain"]
+    # diagnostics: the error head over the field, and the true error of the prediction there
+    o = torch.zeros((n, 11), dtype=torch.float32, device=DEV)
+    ctx.surrogate_infer(_dev(T), _dev(Y), rho_d, e_d, dt, o)
+    o = o.cpu().numpy()
+    hd = np.percentile(o[:, 10], [1, 10, 50, 90])
+    print(f"\nerror head over the field: p1/p10/p50/p90 {hd}; cold {np.percentile(o[~hot, 10], [1, 50, 99])}, "
+          f"hot {np.percentile(o[hot, 10], [1, 50, 99])}")
+    assert g["na"] == int(g["acc"].sum()) and g["na"] > 0
+    assert g["st"]["nqueued"] <= pl["st"]["nqueued"]
+    # accepted cells against the oracle: the false-accept rate on a sample (hot cells first)
+    acc_idx = np.nonzero(g["acc"])[0]
+    hot_acc = acc_idx[hot[acc_idx]]
+    pick = np.concatenate([hot_acc[:100], rng.choice(acc_idx, min(200, acc_idx.size), replace=False)])
+    bad, eT, eY = _errors(h2mech, rho[pick], e[pick], T[pick], Y[:, pick], dt, g["T"][pick], g["Y"][:, pick])
+    far = bad.mean()
+    print(f"\nsurrogate: pairs {t_pairs:.1f} s, train {t_train:.1f} s, loss {losses[0]:.3g} -> {losses[-1]:.3g}; "
+          f"accepted {g['na']}/{n} ({g['na'] / n:.3f}; hot accepted {hot_acc.size}/{int(hot.sum())}); "
+          f"false-accept {bad.sum()}/{pick.size}; max rel err T {eT.max():.2e} Y {eY.max():.2e}; "
+          f"queued plain {pl['st']['nqueued']} gated {g['st']['nqueued']}; "
+          f"ms plain {pl['ms']:.2f} gated {g['ms']:.2f}")
+    assert far <= 0.02
+    # rejected cells took the plain path: identical to the plain step there
+    rej = ~g["acc"]
+    assert np.array_equal(g["T"][rej], pl["T"][rej]) and np.array_equal(g["Y"][:, rej], pl["Y"][:, rej])
+    ctx.close()
