@@ -9,6 +9,10 @@ pristine device copy, flushes L2 (256 MiB write) and advances every cell through
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
 
+A second leg ("gated" in the JSON line) times the same steps with the learned surrogate in
+front of the method (chem_advance_gated), after training it on pairs made by the plain integrator
+(outside the timed region), and reports the accepted fraction and the sampled error vs the oracle.
+
 Under torchrun (N > 1) every rank advances its own field (seed = rank): weak scaling, no
 collective on the data path; the step time is the max over ranks.  `--impl reference` times the
 FP64 CPU oracle (the checker of this library) on bounded stratified samples of the same field.
@@ -27,6 +31,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 import synth  # noqa: E402
+from paper_2510_23993_gb300.shard import max_over_ranks  # noqa: E402
 
 METRIC = "chem cell-steps/s at rel err ≤1e-4 (gated surrogate vs plain GPU), % roofline"
 UNIT = "cell-steps/s"
@@ -51,16 +56,16 @@ CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.ac
 
 
 def _config(n, args):
-    return {"workload": f"reacting sheet {N_EDGE}^3 ({n} cells, 5% reacting), H2-air-shaped mechanism "
+    return {"workload": f"reacting sheet {args.edge}^3 ({n} cells, 5% reacting), H2-air-shaped mechanism "
                         f"9 species / 21 reactions, dt = {DT:g} s, FP32 state, bulk-sparse",
             "cells": n, "dt_s": DT, "rtol": args.rtol, "atol": args.atol,
             "l2": "flushed (256 MiB write) and state restored from a pristine copy inside every step",
             "mechanism_seed": 0, "field_seed": "rank"}
 
 
-def _field(seed):
+def _field(seed, edge=N_EDGE):
     mech = synth.h2_air_mechanism(0)
-    T, p, Y, hot = synth.sheet_field(mech, n=N_EDGE, seed=seed)
+    T, p, Y, hot = synth.sheet_field(mech, n=edge, seed=seed)
     return mech, T.astype(np.float32), p.astype(np.float32), np.ascontiguousarray(Y, dtype=np.float32), hot
 
 
@@ -115,10 +120,10 @@ def run_gpu(args, rank, world, local_rank, dist):
     chem.build()
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    mech, T, p, Y, hot = _field(seed=rank)
+    mech, T, p, Y, hot = _field(seed=rank, edge=args.edge)
     n = T.size
-    ctx = chem.Context(mech, max_cells=n, rtol=args.rtol, atol=args.atol,
-                       flags=chem.CHEM_FLAG_TIMING | chem.CHEM_FLAG_ORDER_RATE)
+    flags = chem.CHEM_FLAG_TIMING | chem.CHEM_FLAG_ORDER_RATE | (chem.CHEM_FLAG_FP64_RATES if args.fp64_rates else 0)
+    ctx = chem.Context(mech, max_cells=max(n, args.train_pairs), rtol=args.rtol, atol=args.atol, flags=flags)
     tT, tp, tY = (torch.from_numpy(a).to(dev) for a in (T, p, Y))
     rho, e = torch.empty_like(tT), torch.empty_like(tT)
     ctx.state_from_TpY(tT, tp, tY, rho, e)
@@ -150,11 +155,7 @@ def run_gpu(args, rank, world, local_rank, dist):
     if dist is not None:
         dist.barrier()
     clk = clocks.stop()
-    ms = ev0.elapsed_time(ev1)
-    if dist is not None:
-        t = torch.tensor([ms], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1), dist)
     total_cells = n * world
     value = total_cells * args.steps / (ms / 1e3)
     for s in stats:
@@ -185,10 +186,7 @@ def run_gpu(args, rank, world, local_rank, dist):
             ctx.advance_host(hT, hp, hY, hrho, he, DT, hsub)
             if i >= args.warmup:
                 wall += time.perf_counter() - t0
-        if dist is not None:
-            t = torch.tensor([wall], dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            wall = float(t.item())
+        wall = max_over_ranks(wall, dist)
         e2e = {"value": total_cells * args.steps / wall, "unit": UNIT,
                "h2d_bytes_per_step": int(n * 4 * (NS + 4)), "d2h_bytes_per_step": int(n * 4 * (NS + 3))}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -199,21 +197,92 @@ def run_gpu(args, rank, world, local_rank, dist):
             "stiff": {"queued_cells": stats[-1]["nqueued"], "bulk_cells": stats[-1]["nbulk"],
                       "substeps_per_stiff_cell": stats[-1]["substeps"] / max(1, stats[-1]["nqueued"]),
                       "newton_per_attempt": stats[-1]["newton"] / max(1, stats[-1]["attempts"])}}
+    if args.gated:
+        line["gated"] = _gated_leg(args, ctx, chem, torch, dev, mech, step_inputs=(tT, tp, tY, rho, e, sub, T0, Y0, flush),
+                                   plain_ms=ms / args.steps, n=n, world=world, dist=dist, rank=rank)
     if rank == 0 and world == 1 and args.cpu_baseline:
         idx, orho, oe, oT, oY, wall, cores = _oracle_sample(mech, T, p, Y, hot, args.cpu_sample, seed=0)
         line["cpu_baseline"] = {"value": len(idx) / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": f"{len(idx)} cells stratified from the same field "
                                           f"({int(hot[idx].sum())} reacting), FP64 Radau IIA rtol 1e-10"}
         line["accuracy"] = _accuracy(ctx, torch, dev, T[idx], p[idx], Y[:, idx], orho, oe, oT, oY)
+        if args.gated:
+            line["gated"]["accuracy"] = _accuracy(ctx, torch, dev, T[idx], p[idx], Y[:, idx], orho, oe, oT, oY,
+                                                  gate_tol=args.gate_tol)
     return line
 
 
-def _accuracy(ctx, torch, dev, T, p, Y, rho, e, T_ref, Y_ref):
-    """Error of the GPU path against the oracle on the CPU-baseline sample (oracle inputs)."""
+def _gated_leg(args, ctx, chem, torch, dev, mech, step_inputs, plain_ms, n, world, dist, rank):
+    """The same steps with the learned surrogate in front of the method (chem_advance_gated).  The
+    surrogate is trained first, outside the timed region, on pairs that the plain integrator makes
+    (FP64-rate mode) from samples over T 300-3200 K, p 1-50 atm, Dirichlet Y, dt 1e-9..1e-6 s."""
+    from paper_2510_23993_gb300 import surrogate
+    tT, tp, tY, rho, e, sub, T0, Y0, flush = step_inputs
+    nbox = 256
+    m = args.train_pairs // nbox
+    Ts, ps, Ys, dts = synth.surrogate_samples(mech, nbox * m, seed=1000 + rank, premix_frac=0.5)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    X, Yt, keep = surrogate.make_pairs(ctx, torch.from_numpy(Ts.astype(np.float32)).to(dev),
+                                       torch.from_numpy(ps.astype(np.float32)).to(dev),
+                                       torch.from_numpy(np.ascontiguousarray(Ys, dtype=np.float32)).to(dev),
+                                       dts[:nbox])
+    torch.cuda.synchronize()
+    t_pairs = time.perf_counter() - t0
+    ctx.surrogate_init(1 + rank)
+    t0 = time.perf_counter()
+    losses = ctx.surrogate_train(X, Yt, epochs=args.train_epochs, batch=4096, lr=1e-3, err_weight=0.1, seed=rank)
+    t_train = time.perf_counter() - t0
+    del X, Yt
+    acc = torch.zeros(n, dtype=torch.uint8, device=dev)
+
+    def gstep(i):
+        tT.copy_(T0)
+        tY.copy_(Y0)
+        flush.fill_(i & 0xFF)
+        ctx.advance_gated(tT, tp, tY, rho, e, DT, args.gate_tol, acc, sub)
+        return ctx.status()
+
+    for i in range(args.warmup):
+        gstep(i)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    stats = [gstep(i) for i in range(args.steps)]
+    ev1.record()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    ms = max_over_ranks(ev0.elapsed_time(ev1), dist)
+    for s in stats:
+        assert s["status"] == 0, s
+    accepted = int(acc.sum().item())
+    return {"value": n * world * args.steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / args.steps,
+            "vs_plain": plain_ms / (ms / args.steps), "gate_tol": args.gate_tol, "accepted_cells": accepted,
+            "accepted_frac": accepted / n, "queued_cells": stats[-1]["nqueued"],
+            "gpu_launches": 4 * args.steps * world,   # surrogate + bulk + queue order + stiff
+            "train": {"pairs": int(keep.sum().item()), "pairs_s": t_pairs, "epochs": args.train_epochs,
+                      "train_s": t_train, "loss_first": losses[0] if losses else None,
+                      "loss_last": losses[-1] if losses else None,
+                      "distribution": "T U[300,3200] K, p U[1,50] atm, Y Dirichlet(0.5) or premix-centred "
+                                      "Dirichlet (half each), dt log-U[1e-9,1e-6] s; targets by the plain "
+                                      "integrator at rtol 1e-6 / atol 1e-11 with FP64 rates"}}
+
+
+def _accuracy(ctx, torch, dev, T, p, Y, rho, e, T_ref, Y_ref, gate_tol=None):
+    """Error of the GPU path (plain, or gated when gate_tol is given) against the oracle on the
+    CPU-baseline sample (oracle inputs)."""
     n = T.size
     a = [torch.from_numpy(np.ascontiguousarray(x)).to(dev) for x in (T, p, Y, rho, e)]
     s = torch.zeros(n, dtype=torch.int32, device=dev)
-    ctx.advance(a[0], a[1], a[2], a[3], a[4], DT, s)
+    nacc = None
+    if gate_tol is None:
+        ctx.advance(a[0], a[1], a[2], a[3], a[4], DT, s)
+    else:
+        acc = torch.zeros(n, dtype=torch.uint8, device=dev)
+        nacc = ctx.advance_gated(a[0], a[1], a[2], a[3], a[4], DT, gate_tol, acc, s)
     ctx.status()
     Tg, Yg = a[0].cpu().numpy().astype(np.float64), a[2].cpu().numpy().astype(np.float64)
     big = Y_ref >= 1e-6
@@ -221,8 +290,11 @@ def _accuracy(ctx, torch, dev, T, p, Y, rho, e, T_ref, Y_ref):
     ab = np.where(~big, np.abs(Yg - Y_ref), 0.0)
     eT = np.abs(Tg - T_ref) / T_ref
     over = (rel.max(0) > 1e-4) | (ab.max(0) > 1e-10) | (eT > 1e-4)
-    return {"cells": int(n), "max_rel_Y": float(rel.max()), "p999_rel_Y": float(np.percentile(rel.max(0), 99.9)),
-            "max_abs_small_Y": float(ab.max()), "max_rel_T": float(eT.max()), "cells_over_1e-4": int(over.sum())}
+    out = {"cells": int(n), "max_rel_Y": float(rel.max()), "p999_rel_Y": float(np.percentile(rel.max(0), 99.9)),
+           "max_abs_small_Y": float(ab.max()), "max_rel_T": float(eT.max()), "cells_over_1e-4": int(over.sum())}
+    if nacc is not None:
+        out["accepted_in_sample"] = int(nacc)
+    return out
 
 
 def _traffic():
@@ -240,7 +312,7 @@ def _traffic():
 
 
 def run_reference(args, world):
-    mech, T, p, Y, hot = _field(seed=0)
+    mech, T, p, Y, hot = _field(seed=0, edge=args.edge)
     walls, ncell = [], 0
     for i in range(args.warmup + args.steps):
         idx, _, _, _, _, wall, cores = _oracle_sample(mech, T, p, Y, hot, args.ref_sample, seed=i)
@@ -255,7 +327,7 @@ def run_reference(args, world):
             "data": "synthetic", "config": _config(T.size, args),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"{args.ref_sample} cells per step, stratified (5% reacting) from the "
-                                       f"{N_EDGE}^3 field; FP64 Radau IIA rtol 1e-10"},
+                                       f"{args.edge}^3 field; FP64 Radau IIA rtol 1e-10"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -265,6 +337,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--edge", type=int, default=N_EDGE, help="field edge (cells); 128 is the benchmark size")
     ap.add_argument("--rtol", type=float, default=1e-5)
     ap.add_argument("--atol", type=float, default=1e-10)
     ap.add_argument("--cpu-sample", type=int, default=8192)
@@ -273,6 +346,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-tune", dest="tune", action="store_false")
     ap.add_argument("--tune-cache", default=None)
+    ap.add_argument("--fp64-rates", action="store_true", help="stiff-cell rates in FP64 (CHEM_FLAG_FP64_RATES)")
+    ap.add_argument("--no-gated", dest="gated", action="store_false", help="skip the gated-surrogate leg")
+    ap.add_argument("--gate-tol", type=float, default=1e-5)
+    ap.add_argument("--train-pairs", type=int, default=262144)
+    ap.add_argument("--train-epochs", type=int, default=40)
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
