@@ -32,22 +32,33 @@ constexpr double kBh1 = 0.7726301276675509;
 constexpr double kBh2 = 0.2273698723324491;
 constexpr double kC2 = 0.5 * (1.0 + kG);
 
-// Per-thread FP64 iteration matrix in shared memory, element (r, c) of thread t at
-// M[(r * NS + c) * B + t]: consecutive threads hit consecutive banks.
+// Per-thread FP64 iteration matrix and one FP64 vector in shared memory: element (r, c) of
+// thread t at M[(r * NS + c) * B + t], vector element k at V[k * B + t], so consecutive threads
+// hit consecutive banks.  The factorisation and the solves index them dynamically in rolled
+// loops: the FP64 pipe, not the instruction count, bounds these loops, and the rolled code keeps
+// the kernel's instruction footprint small enough for the instruction caches.
 template <int NS>
 struct Smem {
   double* M;
+  double* V;
   int t, B;
   __device__ double& mm(int r, int c) const { return M[(r * NS + c) * B + t]; }
+  __device__ double& vv(int k) const { return V[k * B + t]; }
 };
 
-// M = I - hh * J from the FP32 Jacobian in registers (FP64 in shared memory).
+// M = I - hh * J from the FP32 Jacobian in registers (FP64 in shared memory).  The product
+// hh * J is formed in FP32: J carries FP32 rounding already, so the FP64 product would add no
+// accuracy, and it saves NS^2 FP64 multiplies per attempt; the identity is added in FP64.
 template <int NS>
 __device__ __forceinline__ void store_iteration_matrix(const Smem<NS>& s, const float (&J)[NS][NS], double hh) {
+  const float mh = static_cast<float>(-hh);
 #pragma unroll
   for (int r = 0; r < NS; ++r)
 #pragma unroll
-    for (int c = 0; c < NS; ++c) s.mm(r, c) = (r == c ? 1.0 : 0.0) - hh * static_cast<double>(J[r][c]);
+    for (int c = 0; c < NS; ++c) {
+      const double v = static_cast<double>(mh * J[r][c]);
+      s.mm(r, c) = r == c ? 1.0 + v : v;
+    }
 }
 
 // LU with partial pivoting in place (unit-lower L below the diagonal, U above, reciprocal of
@@ -55,19 +66,22 @@ __device__ __forceinline__ void store_iteration_matrix(const Smem<NS>& s, const 
 template <int NS>
 __device__ __forceinline__ bool lu_factor(const Smem<NS>& s, uint64_t* piv) {
   uint64_t pv = 0;
-#pragma unroll
+#pragma unroll 1
   for (int k = 0; k < NS; ++k) {
     int p = k;
     double best = fabs(s.mm(k, k));
-#pragma unroll
+#pragma unroll 1
     for (int i = k + 1; i < NS; ++i) {
       const double v = fabs(s.mm(i, k));
-      if (v > best) { best = v; p = i; }
+      if (v > best) {
+        best = v;
+        p = i;
+      }
     }
     if (!(best > 0.0)) return false;
     pv |= static_cast<uint64_t>(p) << (4 * k);
     if (p != k) {
-#pragma unroll
+#pragma unroll 1
       for (int c = 0; c < NS; ++c) {
         const double t = s.mm(k, c);
         s.mm(k, c) = s.mm(p, c);
@@ -76,45 +90,49 @@ __device__ __forceinline__ bool lu_factor(const Smem<NS>& s, uint64_t* piv) {
     }
     const double inv = 1.0 / s.mm(k, k);
     s.mm(k, k) = inv;
-    double rowk[NS];
-#pragma unroll
-    for (int c = k + 1; c < NS; ++c) rowk[c] = s.mm(k, c);
-#pragma unroll
+#pragma unroll 1
     for (int i = k + 1; i < NS; ++i) {
       const double l = s.mm(i, k) * inv;
       s.mm(i, k) = l;
-#pragma unroll
-      for (int c = k + 1; c < NS; ++c) s.mm(i, c) = fma(-l, rowk[c], s.mm(i, c));
+#pragma unroll 2
+      for (int c = k + 1; c < NS; ++c) s.mm(i, c) = fma(-l, s.mm(k, c), s.mm(i, c));
     }
   }
   *piv = pv;
   return true;
 }
 
+// Solve M x = b with the factors of lu_factor (b in registers, in and out; the permutation and
+// the substitutions run on the shared-memory vector).
 template <int NS>
 __device__ __forceinline__ void lu_solve(const Smem<NS>& s, uint64_t piv, double (&b)[NS]) {
 #pragma unroll
+  for (int k = 0; k < NS; ++k) s.vv(k) = b[k];
+#pragma unroll 1
   for (int k = 0; k < NS; ++k) {
     const int p = static_cast<int>((piv >> (4 * k)) & 15u);
-#pragma unroll
-    for (int j = k + 1; j < NS; ++j) {
-      if (p == j) {
-        const double t = b[k];
-        b[k] = b[j];
-        b[j] = t;
-      }
+    if (p != k) {
+      const double t = s.vv(k);
+      s.vv(k) = s.vv(p);
+      s.vv(p) = t;
     }
   }
-#pragma unroll
-  for (int i = 1; i < NS; ++i)
-#pragma unroll
-    for (int j = 0; j < i; ++j) b[i] = fma(-s.mm(i, j), b[j], b[i]);
-#pragma unroll
-  for (int i = NS - 1; i >= 0; --i) {
-#pragma unroll
-    for (int j = i + 1; j < NS; ++j) b[i] = fma(-s.mm(i, j), b[j], b[i]);
-    b[i] *= s.mm(i, i);
+#pragma unroll 1
+  for (int i = 1; i < NS; ++i) {
+    double acc = s.vv(i);
+#pragma unroll 1
+    for (int j = 0; j < i; ++j) acc = fma(-s.mm(i, j), s.vv(j), acc);
+    s.vv(i) = acc;
   }
+#pragma unroll 1
+  for (int i = NS - 1; i >= 0; --i) {
+    double acc = s.vv(i);
+#pragma unroll 1
+    for (int j = i + 1; j < NS; ++j) acc = fma(-s.mm(i, j), s.vv(j), acc);
+    s.vv(i) = acc * s.mm(i, i);
+  }
+#pragma unroll
+  for (int k = 0; k < NS; ++k) b[k] = s.vv(k);
 }
 
 struct CellCtx {
@@ -140,21 +158,25 @@ __device__ __forceinline__ bool stage_newton(const MechView& m, const Smem<NS>& 
     bool ok;
     Tz = temperature_from_energy<NS>(m, z, c.e0, Tz, &ok);
     if (!ok) return false;
-    float F[NS];
-    if (c.fp64_rates)
-      rates_fp64_fallback<NS>(m, c.rho, Tz, z, F);
-    else
-      rates_safe<NS>(m, c.rho, Tz, z, F);
+    float F[NS], Zf[NS];
+#pragma unroll
+    for (int k = 0; k < NS; ++k) Zf[k] = static_cast<float>(z[k]);
+    bool use64 = c.fp64_rates;
+    // FP32 rates; the FP64 instance (one copy in the code) when they overflow
+    if (!use64) use64 = !rates<NS, float>(m, c.rho, static_cast<float>(Tz), Zf, F);
+    if (use64) rates_fp64_fallback<NS>(m, c.rho, Tz, z, F);
+    const float mhh = static_cast<float>(hh);
     double b[NS];
 #pragma unroll
-    for (int k = 0; k < NS; ++k) b[k] = -((z[k] - yb[k]) - hh * static_cast<double>(F[k]));
+    for (int k = 0; k < NS; ++k) b[k] = (yb[k] - z[k]) + static_cast<double>(mhh * F[k]);
     lu_solve<NS>(s, piv, b);
     float ss = 0.0f;
 #pragma unroll
     for (int k = 0; k < NS; ++k) {
       z[k] += b[k];
-      const float w = c.atol + c.rtol * fabsf(static_cast<float>(z[k]));
-      const float r = static_cast<float>(b[k]) / w;
+      const float bf = static_cast<float>(b[k]);
+      const float w = c.atol + c.rtol * fabsf(Zf[k] + bf);
+      const float r = bf / w;
       ss = fmaf(r, r, ss);
     }
     const double nrm = sqrt(static_cast<double>(ss) * (1.0 / NS));
@@ -186,6 +208,7 @@ __global__ void __launch_bounds__(kStiffBlock) stiff_kernel(const AdvanceArgs<S>
   sm.t = threadIdx.x;
   sm.B = kStiffBlock;
   sm.M = reinterpret_cast<double*>(smem + blob_pad + box_smem_bytes(a.nbox));
+  sm.V = sm.M + NS * NS * kStiffBlock;
 
   const int lane = threadIdx.x & 31;
   const int qn = min(*reinterpret_cast<volatile int*>(&a.ws->qcount), static_cast<int>(a.n));
@@ -382,7 +405,7 @@ __global__ void __launch_bounds__(kStiffBlock) stiff_kernel(const AdvanceArgs<S>
 static unsigned pad128(unsigned b) { return (b + 127u) & ~127u; }
 
 size_t stiff_smem_bytes(int ns, unsigned blob_bytes, int nbox) {
-  return pad128(blob_bytes) + box_smem_bytes(nbox) + static_cast<size_t>(ns) * ns * kStiffBlock * sizeof(double);
+  return pad128(blob_bytes) + box_smem_bytes(nbox) + static_cast<size_t>(ns) * (ns + 1) * kStiffBlock * sizeof(double);
 }
 
 template <int NS, typename S>
