@@ -87,6 +87,14 @@ typedef struct {
  * pass the previous call's output, e.g. in a time-stepping loop). */
 #define CHEM_FLAG_ORDER_RATE 4
 #define CHEM_FLAG_ORDER_PREV 8
+/* chem_params.flags: integrate the stiff cells in two passes.  The first pass gives every queued
+ * cell up to 32 implicit steps and saves the state of the cells it did not finish; those are
+ * then sorted by their estimated remaining steps, (dt - t) / h at the current step size, and the
+ * second pass finishes them, longest first.  This starts the expensive cells early, which the
+ * tail of the persistent stiff kernel needs when the cost order of ORDER_RATE is inaccurate.
+ * Needs 8 * ns + 53 bytes of device memory per cell of max_cells, allocated when the flag is first
+ * set (chem_init or chem_set_params); ignored by chem_advance_noalloc. */
+#define CHEM_FLAG_TWO_PASS 16
 
 /* Counters of the last advance call (see chem_status). */
 typedef struct {

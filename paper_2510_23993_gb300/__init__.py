@@ -24,6 +24,7 @@ CHEM_FLAG_FP64_RATES = 1
 CHEM_FLAG_TIMING = 2
 CHEM_FLAG_ORDER_RATE = 4
 CHEM_FLAG_ORDER_PREV = 8
+CHEM_FLAG_TWO_PASS = 16
 
 _P = ctypes.POINTER
 _c_void_p = ctypes.c_void_p

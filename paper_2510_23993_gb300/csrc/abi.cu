@@ -49,6 +49,12 @@ struct chem_ctx {
   std::vector<double> W;
   std::vector<int8_t> nu_f, nu_r;
   chem::sg::State* sg = nullptr;   // surrogate (surrogate.cu), created by chem_surrogate_init
+  // two-pass stiff integration (CHEM_FLAG_TWO_PASS): continuation state by queue slot
+  double* cont = nullptr;
+  int* cont_list = nullptr;
+  unsigned char* cont_key = nullptr;
+  int* cont_sorted = nullptr;
+  long long cont_cap = 0;
 };
 
 namespace {
@@ -220,9 +226,59 @@ int check_params(const chem_params* p) {
   if (!p) return CHEM_EINVAL;
   if (!(p->rtol > 0 && p->rtol < 1) || !(p->atol > 0 && p->atol < 1) || !std::isfinite(p->T_min) ||
       !(p->bulk_frac > 0) || !(p->y_floor > 0) || p->k_bulk < 1 || p->k_bulk > 64 || p->k_max < 1 ||
-      (p->flags & ~(CHEM_FLAG_FP64_RATES | CHEM_FLAG_TIMING | CHEM_FLAG_ORDER_RATE | CHEM_FLAG_ORDER_PREV)) != 0)
+      (p->flags & ~(CHEM_FLAG_FP64_RATES | CHEM_FLAG_TIMING | CHEM_FLAG_ORDER_RATE | CHEM_FLAG_ORDER_PREV |
+                    CHEM_FLAG_TWO_PASS)) != 0)
     return CHEM_EINVAL;
   return CHEM_OK;
+}
+
+// continuation storage of the two-pass mode, allocated once when the flag is first set
+int ensure_two_pass(chem_ctx* c) {
+  if (!(c->prm.flags & CHEM_FLAG_TWO_PASS) || c->cont) return CHEM_OK;
+  const long long cap = c->max_cells > 0 ? c->max_cells : 1;
+  if (cudaMalloc(&c->cont, static_cast<size_t>(cap * cont_bytes_per_slot(c->ns))) != cudaSuccess ||
+      cudaMalloc(&c->cont_list, sizeof(int) * cap) != cudaSuccess || cudaMalloc(&c->cont_key, cap) != cudaSuccess ||
+      cudaMalloc(&c->cont_sorted, sizeof(int) * cap) != cudaSuccess) {
+    cudaFree(c->cont);
+    cudaFree(c->cont_list);
+    cudaFree(c->cont_key);
+    cudaFree(c->cont_sorted);
+    c->cont = nullptr;
+    c->cont_list = nullptr;
+    c->cont_key = nullptr;
+    c->cont_sorted = nullptr;
+    return CHEM_ENOMEM;
+  }
+  c->cont_cap = cap;
+  return CHEM_OK;
+}
+
+// The stiff phase: one persistent launch, or (two-pass mode) a probe launch, a counting sort of
+// the unfinished cells by remaining work and a continuation launch.
+template <typename S>
+int launch_stiff_phase(chem_ctx* c, AdvanceArgs<S> b, long long n, cudaStream_t st) {
+  auto launch = [&](const AdvanceArgs<S>& x) {
+    if constexpr (sizeof(S) == 4) return launch_stiff_f32(c->ns, x, c->stiff_grid, st);
+    else return launch_stiff_f64(c->ns, x, c->stiff_grid, st);
+  };
+  b.pass = 0;
+  b.cont_cap = 0;
+  b.cont = nullptr;
+  b.cont_list = nullptr;
+  b.cont_key = nullptr;
+  b.cont_sorted = nullptr;
+  if (!(c->prm.flags & CHEM_FLAG_TWO_PASS) || !c->cont || n > c->cont_cap) return launch(b);
+  b.cont_cap = c->cont_cap;
+  b.cont = c->cont;
+  b.cont_list = c->cont_list;
+  b.cont_key = c->cont_key;
+  b.cont_sorted = c->cont_sorted;
+  b.pass = 1;
+  int r = launch(b);
+  if (!r) r = launch_order_queue(c->ws, c->cont_list, c->cont_key, c->cont_sorted, n, st, true);
+  b.pass = 2;
+  if (!r) r = launch(b);
+  return r;
 }
 
 KParams kparams(const chem_params& p) {
@@ -280,17 +336,11 @@ int advance_impl(chem_ctx* ctx, S* T, S* p, S* Y, int64_t ld, const S* rho, cons
     if (timed) cudaEventRecord(ctx->ev[0], st);
     AdvanceArgs<S> b = a;   // the stiff kernel reads the cost-ordered queue when ordering is on
     if (order) b.queue = ctx->queue2;
-    if constexpr (sizeof(S) == 4) {
-      r1 = launch_bulk_f32(ctx->ns, a, bgrid, st);
-      if (!r1 && order) r1 = launch_order_queue(ctx->ws, ctx->queue, ctx->qkey, ctx->queue2, n, st);
-      if (timed && !r1) cudaEventRecord(ctx->ev[1], st);
-      r2 = r1 ? r1 : launch_stiff_f32(ctx->ns, b, ctx->stiff_grid, st);
-    } else {
-      r1 = launch_bulk_f64(ctx->ns, a, bgrid, st);
-      if (!r1 && order) r1 = launch_order_queue(ctx->ws, ctx->queue, ctx->qkey, ctx->queue2, n, st);
-      if (timed && !r1) cudaEventRecord(ctx->ev[1], st);
-      r2 = r1 ? r1 : launch_stiff_f64(ctx->ns, b, ctx->stiff_grid, st);
-    }
+    if constexpr (sizeof(S) == 4) r1 = launch_bulk_f32(ctx->ns, a, bgrid, st);
+    else r1 = launch_bulk_f64(ctx->ns, a, bgrid, st);
+    if (!r1 && order) r1 = launch_order_queue(ctx->ws, ctx->queue, ctx->qkey, ctx->queue2, n, st);
+    if (timed && !r1) cudaEventRecord(ctx->ev[1], st);
+    r2 = r1 ? r1 : launch_stiff_phase<S>(ctx, b, n, st);
     if (timed && !r1 && !r2) cudaEventRecord(ctx->ev[2], st);
     if (r1 == -1 || r2 == -1) return CHEM_EUNSUPPORTED;
     if (r1 || r2) return cuda_fail(static_cast<cudaError_t>(r1 ? r1 : r2), "kernel launch");
@@ -410,14 +460,18 @@ int chem_init(const chem_mechanism* mech, const chem_params* params, int64_t max
   c->stiff_grid = c->sms * spsm;
   for (auto& e : c->ev)
     if (cudaEventCreate(&e) != cudaSuccess) return fail(CHEM_ECUDA);
+  if ((rc = ensure_two_pass(c))) return fail(rc);
   *out = c;
   return CHEM_OK;
 }
 
 int chem_set_params(chem_ctx* ctx, const chem_params* params) {
   if (!ctx || check_params(params)) return CHEM_EINVAL;
+  const chem_params old = ctx->prm;
   ctx->prm = *params;
-  return CHEM_OK;
+  const int rc = ensure_two_pass(ctx);
+  if (rc) ctx->prm = old;
+  return rc;
 }
 
 void chem_destroy(chem_ctx* ctx) {
@@ -439,6 +493,10 @@ void chem_destroy(chem_ctx* ctx) {
   cudaFree(ctx->boxes);
   cudaFree(ctx->box_off);
   surrogate_release(ctx->sg);
+  cudaFree(ctx->cont);
+  cudaFree(ctx->cont_list);
+  cudaFree(ctx->cont_key);
+  cudaFree(ctx->cont_sorted);
   delete ctx;
 }
 
@@ -565,7 +623,7 @@ int chem_advance_boxes(chem_ctx* ctx, void* stream) {
     const int bgrid = static_cast<int>(want < ctx->bulk_grid ? (want < 1 ? 1 : want) : ctx->bulk_grid);
     int r1 = launch_bulk_f32(ctx->ns, a, bgrid, st);
     if (!r1 && order) r1 = launch_order_queue(ctx->ws, ctx->queue, ctx->qkey, ctx->queue2, n, st);
-    int r2 = r1 ? r1 : launch_stiff_f32(ctx->ns, b, ctx->stiff_grid, st);
+    int r2 = r1 ? r1 : launch_stiff_phase<float>(ctx, b, n, st);
     if (r1 == -1 || r2 == -1) return CHEM_EUNSUPPORTED;
     if (r1 || r2) return cuda_fail(static_cast<cudaError_t>(r1 ? r1 : r2), "kernel launch");
   }

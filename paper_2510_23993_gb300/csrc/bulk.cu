@@ -155,10 +155,11 @@ __global__ void __launch_bounds__(kBulkBlock) bulk_kernel(const AdvanceArgs<S> a
 // longest-first order shortens the tail of the persistent stiff kernel, whose duration is set
 // by the cells that start last.
 __global__ void __launch_bounds__(1024) order_queue_kernel(Workspace* ws, const int* queue, const unsigned char* qkey,
-                                                           int* queue_out, long long n) {
+                                                           int* queue_out, long long n, bool continuations) {
   __shared__ int hist[kNumBuckets];
   __shared__ int off[kNumBuckets];
-  const int qn = static_cast<int>(min(static_cast<long long>(*reinterpret_cast<volatile int*>(&ws->qcount)), n));
+  const int* count = continuations ? &ws->cont_count : &ws->qcount;
+  const int qn = static_cast<int>(min(static_cast<long long>(*reinterpret_cast<volatile const int*>(count)), n));
   for (int b = threadIdx.x; b < kNumBuckets; b += blockDim.x) hist[b] = 0;
   __syncthreads();
   for (int i = threadIdx.x; i < qn; i += blockDim.x) atomicAdd(&hist[qkey[i] & (kNumBuckets - 1)], 1);
@@ -178,8 +179,8 @@ __global__ void __launch_bounds__(1024) order_queue_kernel(Workspace* ws, const 
 }
 
 int launch_order_queue(Workspace* ws, const int* queue, const unsigned char* qkey, int* queue_out, long long n,
-                       cudaStream_t s) {
-  order_queue_kernel<<<1, 1024, 0, s>>>(ws, queue, qkey, queue_out, n);
+                       cudaStream_t s, bool continuations) {
+  order_queue_kernel<<<1, 1024, 0, s>>>(ws, queue, qkey, queue_out, n, continuations);
   return static_cast<int>(cudaGetLastError());
 }
 

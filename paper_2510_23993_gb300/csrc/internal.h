@@ -10,7 +10,9 @@ struct Workspace {
   int qcount;                    // cells compacted into the stiff queue by the bulk kernel
   int head;                      // next queue slot handed out by the stiff kernel
   int status;                    // OR of kFlag* bits
-  int pad;
+  int cont_count;                // two-pass mode: cells the first stiff pass left unfinished
+  int head2;                     // two-pass mode: next continuation handed out by the second pass
+  int pad[3];
   unsigned long long nskipped, nbulk, ninvalid, nfailed, substeps, attempts, newton;
 };
 
@@ -55,6 +57,14 @@ struct AdvanceArgs {
   int nbox;                      // 0: flat arrays T, p, Y, rho, e, substeps of n cells, step dt
   const unsigned char* skip;     // [n] or null: cells with skip[g] != 0 are left untouched (their
                                  //   step was taken elsewhere, e.g. by the surrogate)
+  // two-pass stiff integration (0: single pass; 1: probe pass; 2: continuation pass)
+  int pass;
+  long long cont_cap;            // capacity of the continuation arrays (queue slots)
+  double* cont;                  // SoA continuation state by queue slot: y[NS], t, h, T, eta
+                                 //   (each [cont_cap] doubles), then float c_v/R, int nst, int natt
+  int* cont_list;                // [cont_cap] queue slots of the unfinished cells (probe pass)
+  unsigned char* cont_key;       // [cont_cap] their remaining-work bucket
+  int* cont_sorted;              // [cont_cap] the same slots, longest remaining first
 };
 
 constexpr int kMaxBoxes = 4096;
@@ -117,7 +127,12 @@ __host__ __device__ inline unsigned box_smem_bytes(int nbox) { return nbox > 0 ?
 // cost keys of the stiff queue (chem_params.flags bits, see include/chem.h)
 constexpr int kFlagOrderRate = 4;   // bucket of log2(dt * sum_k |dY_k/dt|) at the bulk step
 constexpr int kFlagOrderPrev = 8;   // bucket of log2 of the cell's substep count of the previous call
+constexpr int kFlagTwoPass = 16;    // two-pass stiff integration
 constexpr int kNumBuckets = 64;
+constexpr int kProbeAttempts = 32;  // implicit steps per cell in the probe pass
+
+// bytes of continuation state per queue slot
+__host__ __device__ constexpr long long cont_bytes_per_slot(int ns) { return 8LL * (ns + 4) + 12; }
 
 constexpr int kBulkBlock = 128;
 constexpr int kStiffBlock = 128;
@@ -130,7 +145,7 @@ int launch_stiff_f64(int ns, const AdvanceArgs<double>& a, int grid, cudaStream_
 size_t stiff_smem_bytes(int ns, unsigned blob_bytes, int nbox);
 // counting sort of the queue by cost bucket, most expensive first: queue -> queue_out
 int launch_order_queue(Workspace* ws, const int* queue, const unsigned char* qkey, int* queue_out,
-                       long long n, cudaStream_t s);
+                       long long n, cudaStream_t s, bool continuations = false);
 size_t bulk_smem_bytes(unsigned blob_bytes, int nbox);
 int stiff_occupancy(int ns, unsigned blob_bytes, int* blocks_per_sm);
 int bulk_occupancy(int ns, bool f64, unsigned blob_bytes, int* blocks_per_sm);

@@ -263,6 +263,12 @@ extern "C" int chem_advance_noalloc(const chem_mechanism* mech, const chem_param
     a.box_off = nullptr;
     a.nbox = 0;
     a.skip = nullptr;
+    a.pass = 0;   // single pass: the two-pass mode's continuation storage is not part of the scratch
+    a.cont_cap = 0;
+    a.cont = nullptr;
+    a.cont_list = nullptr;
+    a.cont_key = nullptr;
+    a.cont_sorted = nullptr;
     int bpsm = 1, spsm = 1;
     if (bulk_occupancy(mech->ns, false, bytes, &bpsm) != 0 || bpsm < 1) bpsm = 1;
     if (stiff_occupancy(mech->ns, bytes, &spsm) != 0 || spsm < 1) spsm = 1;

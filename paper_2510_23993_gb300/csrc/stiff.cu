@@ -211,13 +211,20 @@ __global__ void __launch_bounds__(kStiffBlock) stiff_kernel(const AdvanceArgs<S>
   sm.V = sm.M + NS * NS * kStiffBlock;
 
   const int lane = threadIdx.x & 31;
-  const int qn = min(*reinterpret_cast<volatile int*>(&a.ws->qcount), static_cast<int>(a.n));
+  // probe and single passes take cells from the stiff queue; the continuation pass takes the
+  // queue slots the probe pass left unfinished, in their sorted order
+  const int pass = a.pass;
+  const int qn = pass == 2 ? min(*reinterpret_cast<volatile int*>(&a.ws->cont_count), static_cast<int>(a.n))
+                           : min(*reinterpret_cast<volatile int*>(&a.ws->qcount), static_cast<int>(a.n));
+  int* head = pass == 2 ? &a.ws->head2 : &a.ws->head;
+  const long long cc = a.cont_cap;
+  double* const cst = a.cont;   // continuation state, SoA by queue slot
   CellCtx c;
   c.rtol = a.prm.rtol;
   c.atol = a.prm.atol;
   c.fp64_rates = (a.prm.flags & 1) != 0;
 
-  int cell = -1;
+  int cell = -1, qpos = -1;
   bool done = false;
   double dt = 0.0;
   double y[NS], t = 0.0, h = 0.0, Tc = 0.0;
@@ -234,33 +241,48 @@ __global__ void __launch_bounds__(kStiffBlock) stiff_kernel(const AdvanceArgs<S>
     if (needm) {
       const int leader = __ffs(needm) - 1;
       int base = 0;
-      if (lane == leader) base = atomicAdd(&a.ws->head, __popc(needm));
+      if (lane == leader) base = atomicAdd(head, __popc(needm));
       base = __shfl_sync(0xffffffffu, base, leader);
       if (need) {
         const int q = base + __popc(needm & ((1u << lane) - 1u));
         if (q < qn) {
-          cell = a.queue[q];
+          qpos = pass == 2 ? a.cont_sorted[q] : q;
+          cell = a.queue[qpos];
           const CellRef<S> cr = locate(a, soff, cell);
           const long long i = cr.i;
           dt = cr.dt;
           c.rho = static_cast<float>(cr.rho[i]);
           c.e0 = static_cast<double>(cr.e[i]);
+          if (pass == 2) {   // resume where the probe pass stopped
 #pragma unroll
-          for (int k = 0; k < NS; ++k) y[k] = static_cast<double>(cr.Y[k * cr.ld + i]);
-          bool ok;
-          double cvd;
-          Tc = temperature_from_energy<NS>(m, y, c.e0, static_cast<double>(cr.T[i]), &ok, &cvd);
-          cvR = static_cast<float>(cvd);
-          t = 0.0;
-          nst = 0;
-          natt = 0;
-          h = 1e-6 * dt;   // the controller grows it by up to 5x per accepted step
-          eta_cell = 1.0;
-          if (!ok) {       // temperature not invertible: fail the cell right away
-            cr.sub[i] = -1;
-            ++c_fail;
-            flags |= kFlagTemp;
-            cell = -1;
+            for (int k = 0; k < NS; ++k) y[k] = cst[k * cc + qpos];
+            t = cst[NS * cc + qpos];
+            h = cst[(NS + 1) * cc + qpos];
+            Tc = cst[(NS + 2) * cc + qpos];
+            eta_cell = cst[(NS + 3) * cc + qpos];
+            const float* cf = reinterpret_cast<const float*>(cst + (NS + 4) * cc);
+            const int* ci = reinterpret_cast<const int*>(cf + cc);
+            cvR = cf[qpos];
+            nst = ci[qpos];
+            natt = ci[cc + qpos];
+          } else {
+#pragma unroll
+            for (int k = 0; k < NS; ++k) y[k] = static_cast<double>(cr.Y[k * cr.ld + i]);
+            bool ok;
+            double cvd;
+            Tc = temperature_from_energy<NS>(m, y, c.e0, static_cast<double>(cr.T[i]), &ok, &cvd);
+            cvR = static_cast<float>(cvd);
+            t = 0.0;
+            nst = 0;
+            natt = 0;
+            h = 1e-6 * dt;   // the controller grows it by up to 5x per accepted step
+            eta_cell = 1.0;
+            if (!ok) {       // temperature not invertible: fail the cell right away
+              cr.sub[i] = -1;
+              ++c_fail;
+              flags |= kFlagTemp;
+              cell = -1;
+            }
           }
         } else {
           done = true;
@@ -359,6 +381,26 @@ __global__ void __launch_bounds__(kStiffBlock) stiff_kernel(const AdvanceArgs<S>
       if (t + h > dt) h = dt - t;
       if (h < 1e-24 * dt || h < 1e-30) { failed = true; flags |= kFlagNoConv; }
       if (nst >= a.prm.k_max || natt >= 4 * a.prm.k_max) { failed = true; flags |= kFlagMaxSteps; }
+    }
+    if (!finished && !failed && pass == 1 && natt >= kProbeAttempts) {
+      // probe pass: park the cell with its integration state and the remaining-work estimate
+#pragma unroll
+      for (int k = 0; k < NS; ++k) cst[k * cc + qpos] = y[k];
+      cst[NS * cc + qpos] = t;
+      cst[(NS + 1) * cc + qpos] = h;
+      cst[(NS + 2) * cc + qpos] = Tc;
+      cst[(NS + 3) * cc + qpos] = eta_cell;
+      float* cf = reinterpret_cast<float*>(cst + (NS + 4) * cc);
+      int* ci = reinterpret_cast<int*>(cf + cc);
+      cf[qpos] = cvR;
+      ci[qpos] = nst;
+      ci[cc + qpos] = natt;
+      const int pos = atomicAdd(&a.ws->cont_count, 1);
+      a.cont_list[pos] = qpos;
+      const float rest = static_cast<float>((dt - t) / h);   // steps left at the current step size
+      a.cont_key[pos] = static_cast<unsigned char>(fminf(fmaxf(4.0f * __log2f(rest + 1.0f), 0.0f),
+                                                         static_cast<float>(kNumBuckets - 1)));
+      cell = -1;
     }
     if (finished) {
       const CellRef<S> cr = locate(a, soff, cell);   // recomputed: keeps the loop's registers free

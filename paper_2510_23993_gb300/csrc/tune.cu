@@ -2,8 +2,8 @@
 //
 // The paper tuned its bulk-step count (K_max = 5) and its bulk-to-sparse threshold by hand
 // (Sec. 3.2, App. D).  Here the knobs are the explicit bulk substeps per cell (k_bulk), the
-// order in which stiff cells are handed to the persistent kernel, and the resident blocks per
-// SM of both kernels.  The tuner times chem_advance on the caller's field for each candidate
+// order in which stiff cells are handed to the persistent kernel (none, by rate, by rate with the
+// two-pass probe/continuation schedule), and the resident blocks per SM of both kernels.  The tuner times chem_advance on the caller's field for each candidate
 // (coordinate descent, best of two repetitions, inputs restored between trials), keeps the
 // fastest, and can cache the choice in a text file keyed by mechanism shape, field size and GPU.
 #include <cmath>
@@ -91,12 +91,15 @@ extern "C" int chem_tune(chem_ctx* ctx, float* T, float* p, float* Y, int64_t ld
   auto apply = [&](const Choice& c) {
     chem_params p = prm0;
     p.k_bulk = c.k_bulk;
-    p.flags = (prm0.flags & ~(CHEM_FLAG_ORDER_RATE | CHEM_FLAG_ORDER_PREV)) | c.order_flags;
-    chem_set_params(ctx, &p);
+    p.flags = (prm0.flags & ~(CHEM_FLAG_ORDER_RATE | CHEM_FLAG_ORDER_PREV | CHEM_FLAG_TWO_PASS)) | c.order_flags;
+    if (chem_set_params(ctx, &p) != CHEM_OK) {   // two-pass storage unavailable: keep the one-pass order
+      p.flags &= ~CHEM_FLAG_TWO_PASS;
+      chem_set_params(ctx, &p);
+    }
     ctx_set_launch(ctx, sms * c.bulk_bpsm, sms * c.stiff_bpsm);
   };
-  Choice best{prm0.k_bulk, prm0.flags & (CHEM_FLAG_ORDER_RATE | CHEM_FLAG_ORDER_PREV), bulk_grid0 / sms,
-              stiff_grid0 / sms};
+  Choice best{prm0.k_bulk, prm0.flags & (CHEM_FLAG_ORDER_RATE | CHEM_FLAG_ORDER_PREV | CHEM_FLAG_TWO_PASS),
+              bulk_grid0 / sms, stiff_grid0 / sms};
   if (cache_lookup(cache_path, key, &best)) {
     apply(best);
     out->k_bulk = best.k_bulk;
@@ -164,7 +167,7 @@ extern "C" int chem_tune(chem_ctx* ctx, float* T, float* p, float* Y, int64_t ld
       c.stiff_bpsm = s;
       consider(c);
     }
-  for (int ord : {0, static_cast<int>(CHEM_FLAG_ORDER_RATE)})
+  for (int ord : {0, static_cast<int>(CHEM_FLAG_ORDER_RATE), static_cast<int>(CHEM_FLAG_ORDER_RATE | CHEM_FLAG_TWO_PASS)})
     if (ord != best.order_flags) {
       Choice c = best;
       c.order_flags = ord;

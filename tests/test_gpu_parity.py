@@ -271,6 +271,25 @@ def test_single_cell_and_determinism(h2mech):
     ctx.close()
 
 
+@pytest.mark.parametrize("order", [0, chem.CHEM_FLAG_ORDER_RATE])
+def test_two_pass_equals_single_pass(h2mech, order):
+    """The two-pass stiff phase parks unfinished cells with their full integration state and
+    resumes them later: every cell's result and substep count are bit-identical, and so are the
+    counters of attempts and Newton iterations."""
+    T, p, Y, hot = synth.sheet_field(h2mech, n=24, seed=9, frac=0.08)
+    T, p, Y, rho, e = _inputs32(h2mech, T, p, Y)
+    ctx = chem.Context(h2mech, max_cells=T.size, flags=order)
+    rc, st1, T1, p1, Y1, s1 = _run(ctx, T, p, Y, rho, e, 1e-8)
+    ctx.set_params(flags=order | chem.CHEM_FLAG_TWO_PASS)
+    rc2, st2, T2, p2, Y2, s2 = _run(ctx, T, p, Y, rho, e, 1e-8)
+    assert rc == 0 and rc2 == 0
+    assert (s1 > 1 + 32).sum() > 10   # some cells outlive the probe pass
+    assert np.array_equal(T1, T2) and np.array_equal(Y1, Y2) and np.array_equal(p1, p2) and np.array_equal(s1, s2)
+    for k in ("nqueued", "substeps", "attempts", "newton", "nfailed"):
+        assert st1[k] == st2[k], k
+    ctx.close()
+
+
 def test_host_entry_point_matches_device(h2mech):
     T, p, Y, hot = synth.sheet_field(h2mech, n=10, seed=8)
     T, p, Y, rho, e = _inputs32(h2mech, T, p, Y)
