@@ -23,6 +23,7 @@ import json
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -85,9 +86,8 @@ class ClockSampler:
         self.proc = None
         self.path = None
         try:
-            self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
-            self.f = open(self.path, "w")
+            fd, self.path = tempfile.mkstemp(prefix="clocks_bench_", suffix=".csv")
+            self.f = os.fdopen(fd, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={CLOCK_QUERY}", "--format=csv,noheader,nounits",
                                           "-lms", "200", "-i", str(gpu_index)], stdout=self.f,
                                          stderr=subprocess.DEVNULL)
@@ -104,6 +104,7 @@ class ClockSampler:
             self.proc.kill()
         self.f.close()
         rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.count(",") >= 8]
+        os.unlink(self.path)
         if not rows:
             return None
         sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
@@ -122,7 +123,8 @@ def run_gpu(args, rank, world, local_rank, dist):
     dev = torch.device("cuda", local_rank)
     mech, T, p, Y, hot = _field(seed=rank, edge=args.edge)
     n = T.size
-    flags = chem.CHEM_FLAG_TIMING | chem.CHEM_FLAG_ORDER_RATE | (chem.CHEM_FLAG_FP64_RATES if args.fp64_rates else 0)
+    flags = chem.CHEM_FLAG_TIMING | chem.CHEM_FLAG_ORDER_RATE | (chem.CHEM_FLAG_FP64_RATES if args.fp64_rates else 0) \
+        | (chem.CHEM_FLAG_TWO_PASS if args.two_pass else 0)
     ctx = chem.Context(mech, max_cells=max(n, args.train_pairs), rtol=args.rtol, atol=args.atol, flags=flags)
     tT, tp, tY = (torch.from_numpy(a).to(dev) for a in (T, p, Y))
     rho, e = torch.empty_like(tT), torch.empty_like(tT)
@@ -189,10 +191,12 @@ def run_gpu(args, rank, world, local_rank, dist):
         wall = max_over_ranks(wall, dist)
         e2e = {"value": total_cells * args.steps / wall, "unit": UNIT,
                "h2d_bytes_per_step": int(n * 4 * (NS + 4)), "d2h_bytes_per_step": int(n * 4 * (NS + 3))}
+    # kernels per step: bulk, queue order, stiff (two-pass: + continuation order + second stiff launch)
+    per_step = 5 if ctx.params.flags & chem.CHEM_FLAG_TWO_PASS else 3
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-            "config": _config(n, args), "roofline": roof, "e2e": e2e, "gpu_launches": 3 * args.steps * world,   # bulk + queue order + stiff
+            "config": _config(n, args), "roofline": roof, "e2e": e2e, "gpu_launches": per_step * args.steps * world,
             "clocks": clk, "tuned": tuned,
             "stiff": {"queued_cells": stats[-1]["nqueued"], "bulk_cells": stats[-1]["nbulk"],
                       "substeps_per_stiff_cell": stats[-1]["substeps"] / max(1, stats[-1]["nqueued"]),
@@ -262,7 +266,7 @@ def _gated_leg(args, ctx, chem, torch, dev, mech, step_inputs, plain_ms, n, worl
     return {"value": n * world * args.steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / args.steps,
             "vs_plain": plain_ms / (ms / args.steps), "gate_tol": args.gate_tol, "accepted_cells": accepted,
             "accepted_frac": accepted / n, "queued_cells": stats[-1]["nqueued"],
-            "gpu_launches": 4 * args.steps * world,   # surrogate + bulk + queue order + stiff
+            "gpu_launches": (1 + (5 if ctx.params.flags & chem.CHEM_FLAG_TWO_PASS else 3)) * args.steps * world,
             "train": {"pairs": int(keep.sum().item()), "pairs_s": t_pairs, "epochs": args.train_epochs,
                       "train_s": t_train, "loss_first": losses[0] if losses else None,
                       "loss_last": losses[-1] if losses else None,
@@ -298,17 +302,19 @@ def _accuracy(ctx, torch, dev, T, p, Y, rho, e, T_ref, Y_ref, gate_tol=None):
 
 
 def _traffic():
-    """DRAM bytes per launch of the stiff kernel from the committed ncu summary, if it was taken on
-    the current source of the kernel (else null)."""
-    path = os.path.join(ROOT, "profiles", "stiff_kernel_traffic.json")
+    """DRAM bytes of the stiff phase per step (its one or two stiff-kernel launches) from the
+    committed ncu summary, if that was taken on the current source of the kernel (else null)."""
+    path = os.path.join(ROOT, "profiles", "stiff_phase_traffic_sheet128.txt")
     if not os.path.exists(path):
         return None
-    rec = json.load(open(path))
+    rec = dict(line.split(":", 1) for line in open(path).read().splitlines() if ":" in line)
     src = os.path.join(ROOT, "paper_2510_23993_gb300", "csrc")
     h = hashlib.sha256()
-    for f in ("stiff.cu", "chem_device.cuh"):
+    for f in ("stiff.cu", "chem_device.cuh", "internal.h"):
         h.update(open(os.path.join(src, f), "rb").read())
-    return rec.get("bytes_per_launch") if rec.get("source_sha256") == h.hexdigest() else None
+    if rec.get("source_sha256", "").strip() != h.hexdigest():
+        return None
+    return float(rec["dram_bytes_per_step"])
 
 
 def run_reference(args, world):
@@ -347,6 +353,8 @@ def main():
     ap.add_argument("--no-tune", dest="tune", action="store_false")
     ap.add_argument("--tune-cache", default=None)
     ap.add_argument("--fp64-rates", action="store_true", help="stiff-cell rates in FP64 (CHEM_FLAG_FP64_RATES)")
+    ap.add_argument("--two-pass", action="store_true", help="two-pass stiff schedule without tuning (the tuner "
+                                                              "chooses it otherwise)")
     ap.add_argument("--no-gated", dest="gated", action="store_false", help="skip the gated-surrogate leg")
     ap.add_argument("--gate-tol", type=float, default=1e-5)
     ap.add_argument("--train-pairs", type=int, default=262144)

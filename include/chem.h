@@ -258,8 +258,8 @@ int chem_tc_gemm(const float *A, int64_t sam, int64_t sak, const float *B, int64
                  int32_t epi, int32_t ksplit, int32_t *status, void *stream);
 
 /* ---------------------------------------------------------------------------------------------
- * Learned surrogate of the chemistry step with a per-cell error gate.  The paper names machine
- * learning for the chemistry as future work (Sec. 6); it has no counterpart there.  The network
+ * Learned surrogate of the chemistry step with a per-cell error gate.  The paper has no
+ * counterpart (its outlook, Sec. 6, mentions machine learning only for performance prediction).  The network
  * (compiled for ns = 9) maps x = (T, ln p, ln dt, ln(Y_k + 1e-6)), standardised, through four
  * GELU layers of 128 to ns + 2 outputs: the standardised encodings a = asinh(u / 1e-8) of
  * u_k = ln((Y1_k + 1e-6) / (max(Y_k, 0) + 1e-6)) and u_T = ln(T1 / T) for the state (Y1, T1)

@@ -3,9 +3,9 @@
 Only the tests, `__graft_entry__.smoke()` and the CPU-baseline leg of `bench.py` may import
 this module.  It shares no code with the CUDA library.
 
-The paper leaves machine learning for the chemistry step as future work (Sec. 6) and defines no
-network; what is computed here is the surrogate as the library's C interface documents it,
-written out plainly in numpy FP64:
+The paper defines no learned surrogate (its outlook, Sec. 6, mentions machine learning only for
+performance prediction); what is computed here is the surrogate as the library's C interface
+documents it, written out plainly in numpy FP64:
 
 * features x = (T, ln p, ln dt, ln(max(Y_k, 0) + 1e-6)), standardised with the stored mean and
   standard deviation;
