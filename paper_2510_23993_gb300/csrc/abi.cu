@@ -48,6 +48,7 @@ struct chem_ctx {
   // host copies of the stoichiometry (the surrogate's conservation constraints)
   std::vector<double> W;
   std::vector<int8_t> nu_f, nu_r;
+  bool large = false;              // sparse table layout, one warp per cell (large.cu)
   chem::sg::State* sg = nullptr;   // surrogate (surrogate.cu), created by chem_surrogate_init
   // two-pass stiff integration (CHEM_FLAG_TWO_PASS): continuation state by queue slot
   double* cont = nullptr;
@@ -70,48 +71,79 @@ unsigned align16(unsigned x) { return (x + 15u) & ~15u; }
 bool compiled_ns(int ns) { return ns == 9; }
 
 // Host-side packing of the mechanism into the device blob layout of chem_device.cuh.
-int pack_mechanism(const chem_mechanism* m, std::vector<unsigned char>& out, int* ntb_out) {
+// Host-side packing of the mechanism into the device blob layout of chem_device.cuh.  The dense
+// layout (ns <= 15) holds full stoichiometric rows and FP64 copies of the rate tables; the large
+// layout (large.cu) holds packed sparse stoichiometry and a species -> reaction index instead, and
+// keeps the thermo regimes below / above the fit range in a tail that is not staged.
+int pack_mechanism(const chem_mechanism* m, std::vector<unsigned char>& out, int* ntb_out, bool large = false) {
   const int ns = m->ns, nr = m->nr;
   const int nsp = (ns + 3) & ~3;
   int ntb = 0;
   for (int r = 0; r < nr; ++r) ntb += m->third_body[r] ? 1 : 0;
+  int nnz = 0;
+  for (int r = 0; r < nr; ++r)
+    for (int k = 0; k < ns; ++k) nnz += (m->nu_r[r * ns + k] != m->nu_f[r * ns + k]) ? 1 : 0;
   MechHdr h{};
   h.ns = ns;
   h.nr = nr;
   h.ntb = ntb;
   h.nsp = nsp;
+  h.large = large ? 1 : 0;
+  h.nnz = nnz;
   const double T_lo = m->thermo[7], T_hi = m->thermo[8];
   h.T_lo = static_cast<float>(T_lo);
   h.T_hi = static_cast<float>(T_hi);
   h.lnP0R = static_cast<float>(std::log(kP0 / kR));
+  const int nreg = large ? 1 : 3;   // regimes of gam / hco in the staged part
   unsigned off = align16(sizeof(MechHdr));
   h.off_arr = off; off = align16(off + 16u * nr);
-  h.off_nuf = off; off = align16(off + 4u * nr * nsp);
-  h.off_nur = off; off = align16(off + 4u * nr * nsp);
-  h.off_dnu = off; off = align16(off + 4u * nr * nsp);
+  if (!large) {
+    h.off_nuf = off; off = align16(off + 4u * nr * nsp);
+    h.off_nur = off; off = align16(off + 4u * nr * nsp);
+    h.off_dnu = off; off = align16(off + 4u * nr * nsp);
+  }
   h.off_eff = off; off = align16(off + 4u * (ntb > 0 ? ntb : 1) * nsp);
   h.off_rinfo = off; off = align16(off + 4u * nr);
   h.off_W = off; off = align16(off + 4u * nsp);
   h.off_invW = off; off = align16(off + 4u * nsp);
-  h.off_gam = off; off = align16(off + 4u * 3 * nr * 8);
-  h.off_hco = off; off = align16(off + 4u * 3 * nr * 8);
+  h.off_gam = off; off = align16(off + 4u * nreg * nr * 8);
+  h.off_hco = off; off = align16(off + 4u * nreg * nr * 8);
   h.off_hsp = off; off = align16(off + 4u * 3 * ns * 8);
   h.off_e64 = off; off = align16(off + 8u * 3 * ns * 8);
-  h.off_arr64 = off; off = align16(off + 8u * 4 * nr);
-  h.off_gam64 = off; off = align16(off + 8u * 3 * nr * 8);
-  h.off_eff64 = off; off = align16(off + 8u * (ntb > 0 ? ntb : 1) * nsp);
+  if (!large) {
+    h.off_arr64 = off; off = align16(off + 8u * 4 * nr);
+    h.off_gam64 = off; off = align16(off + 8u * 3 * nr * 8);
+    h.off_eff64 = off; off = align16(off + 8u * (ntb > 0 ? ntb : 1) * nsp);
+    h.prefix = off;
+  } else {
+    h.off_sto = off; off = align16(off + 8u * nr);
+    h.off_cptr = off; off = align16(off + 4u * (ns + 1));
+    h.off_cent = off; off = align16(off + 4u * nnz);
+    h.prefix = off;
+    h.off_gamg = off; off = align16(off + 4u * 3 * nr * 8);
+    h.off_hcog = off; off = align16(off + 4u * 3 * nr * 8);
+  }
   h.bytes = off;
   out.assign(off, 0);
   std::memcpy(out.data(), &h, sizeof(h));
   auto F = [&](int o) { return reinterpret_cast<float*>(out.data() + o); };
   float* arr = F(h.off_arr);
-  float *nuf = F(h.off_nuf), *nur = F(h.off_nur), *dnu = F(h.off_dnu), *eff = F(h.off_eff);
+  float *eff = F(h.off_eff);
   int* rinfo = reinterpret_cast<int*>(out.data() + h.off_rinfo);
-  float *W = F(h.off_W), *invW = F(h.off_invW), *gam = F(h.off_gam), *hco = F(h.off_hco), *hsp = F(h.off_hsp);
+  float *W = F(h.off_W), *invW = F(h.off_invW), *hsp = F(h.off_hsp);
   double* e64 = reinterpret_cast<double*>(out.data() + h.off_e64);
-  double* arr64 = reinterpret_cast<double*>(out.data() + h.off_arr64);
-  double* gam64 = reinterpret_cast<double*>(out.data() + h.off_gam64);
-  double* eff64 = reinterpret_cast<double*>(out.data() + h.off_eff64);
+  // dense layout: the rows and the FP64 copies; large layout: all regimes of gam / hco go to the
+  // unstaged tail, regime 1 is copied into the staged part afterwards
+  std::vector<float> scratch_rows(large ? 3u * nr * nsp : 0u);
+  std::vector<double> scratch64(large ? 4u * nr + 3u * nr * 8 + (ntb > 0 ? ntb : 1) * nsp : 0u);
+  float *nuf = large ? scratch_rows.data() : F(h.off_nuf);
+  float *nur = large ? scratch_rows.data() + nr * nsp : F(h.off_nur);
+  float *dnu = large ? scratch_rows.data() + 2 * nr * nsp : F(h.off_dnu);
+  float *gam = large ? F(h.off_gamg) : F(h.off_gam);
+  float *hco = large ? F(h.off_hcog) : F(h.off_hco);
+  double* arr64 = large ? scratch64.data() : reinterpret_cast<double*>(out.data() + h.off_arr64);
+  double* gam64 = large ? scratch64.data() + 4 * nr : reinterpret_cast<double*>(out.data() + h.off_gam64);
+  double* eff64 = large ? scratch64.data() + 4 * nr + 3 * nr * 8 : reinterpret_cast<double*>(out.data() + h.off_eff64);
   for (int k = 0; k < ns; ++k) {
     W[k] = static_cast<float>(m->W[k]);
     invW[k] = static_cast<float>(1.0 / m->W[k]);
@@ -191,12 +223,44 @@ int pack_mechanism(const chem_mechanism* m, std::vector<unsigned char>& out, int
       }
     }
   }
+  if (large) {
+    // regime-1 copies into the staged part
+    std::memcpy(F(h.off_gam), gam + nr * 8, 4u * nr * 8);
+    std::memcpy(F(h.off_hco), hco + nr * 8, 4u * nr * 8);
+    // packed sparse stoichiometry: up to 3 (species, coefficient) pairs per side, 9 bits each
+    int2* sto = reinterpret_cast<int2*>(out.data() + h.off_sto);
+    for (int r = 0; r < nr; ++r) {
+      int packed[2] = {0, 0}, cnt[2] = {0, 0};
+      for (int k = 0; k < ns; ++k)
+        for (int side = 0; side < 2; ++side) {
+          const int c = side == 0 ? m->nu_f[r * ns + k] : m->nu_r[r * ns + k];
+          if (c == 0) continue;
+          if (cnt[side] >= 3 || c > 3 || k > 127) return CHEM_EUNSUPPORTED;
+          packed[side] |= (k | (c << 7)) << (9 * cnt[side]);
+          ++cnt[side];
+        }
+      sto[r] = make_int2(packed[0], packed[1]);
+    }
+    // species -> (reaction, dnu), reactions in increasing order
+    int* cptr = reinterpret_cast<int*>(out.data() + h.off_cptr);
+    int* cent = reinterpret_cast<int*>(out.data() + h.off_cent);
+    int e = 0;
+    for (int k = 0; k < ns; ++k) {
+      cptr[k] = e;
+      for (int r = 0; r < nr; ++r) {
+        const int d = m->nu_r[r * ns + k] - m->nu_f[r * ns + k];
+        if (d != 0) cent[e++] = (r & 0xFFFF) | (d * 65536);
+      }
+    }
+    cptr[ns] = e;
+    if (nr > 65535) return CHEM_EUNSUPPORTED;
+  }
   *ntb_out = ntb;
   return CHEM_OK;
 }
 
 int check_mechanism(const chem_mechanism* m) {
-  if (!m || m->ns < 1 || m->ns > 15 || m->nr < 1 || !m->W || !m->thermo || !m->nu_f || !m->nu_r || !m->A ||
+  if (!m || m->ns < 1 || m->ns > 127 || m->nr < 1 || !m->W || !m->thermo || !m->nu_f || !m->nu_r || !m->A ||
       !m->b || !m->Ea || !m->reversible || !m->third_body)
     return CHEM_EINVAL;
   bool any_tb = false;
@@ -234,7 +298,8 @@ int check_params(const chem_params* p) {
 
 // continuation storage of the two-pass mode, allocated once when the flag is first set
 int ensure_two_pass(chem_ctx* c) {
-  if (!(c->prm.flags & CHEM_FLAG_TWO_PASS) || c->cont) return CHEM_OK;
+  // the warp-per-cell path of large mechanisms runs the single-pass schedule (flag ignored)
+  if (!(c->prm.flags & CHEM_FLAG_TWO_PASS) || c->cont || c->large) return CHEM_OK;
   const long long cap = c->max_cells > 0 ? c->max_cells : 1;
   if (cudaMalloc(&c->cont, static_cast<size_t>(cap * cont_bytes_per_slot(c->ns))) != cudaSuccess ||
       cudaMalloc(&c->cont_list, sizeof(int) * cap) != cudaSuccess || cudaMalloc(&c->cont_key, cap) != cudaSuccess ||
@@ -336,11 +401,24 @@ int advance_impl(chem_ctx* ctx, S* T, S* p, S* Y, int64_t ld, const S* rho, cons
     if (timed) cudaEventRecord(ctx->ev[0], st);
     AdvanceArgs<S> b = a;   // the stiff kernel reads the cost-ordered queue when ordering is on
     if (order) b.queue = ctx->queue2;
-    if constexpr (sizeof(S) == 4) r1 = launch_bulk_f32(ctx->ns, a, bgrid, st);
-    else r1 = launch_bulk_f64(ctx->ns, a, bgrid, st);
-    if (!r1 && order) r1 = launch_order_queue(ctx->ws, ctx->queue, ctx->qkey, ctx->queue2, n, st);
-    if (timed && !r1) cudaEventRecord(ctx->ev[1], st);
-    r2 = r1 ? r1 : launch_stiff_phase<S>(ctx, b, n, st);
+    if (ctx->large) {   // one warp per cell (FP32 state only)
+      if constexpr (sizeof(S) == 4) {
+        const long long wb = (n + 7) / 8;   // bulk CTAs of 8 warps
+        const int lgrid = static_cast<int>(wb < ctx->bulk_grid ? (wb < 1 ? 1 : wb) : ctx->bulk_grid);
+        r1 = launch_bulk_lg(ctx->ns, ctx->nr, ctx->ntb, a, lgrid, st);
+        if (!r1 && order) r1 = launch_order_queue(ctx->ws, ctx->queue, ctx->qkey, ctx->queue2, n, st);
+        if (timed && !r1) cudaEventRecord(ctx->ev[1], st);
+        r2 = r1 ? r1 : launch_stiff_lg(ctx->ns, ctx->nr, ctx->ntb, b, ctx->stiff_grid, st);
+      } else {
+        return CHEM_EUNSUPPORTED;
+      }
+    } else {
+      if constexpr (sizeof(S) == 4) r1 = launch_bulk_f32(ctx->ns, a, bgrid, st);
+      else r1 = launch_bulk_f64(ctx->ns, a, bgrid, st);
+      if (!r1 && order) r1 = launch_order_queue(ctx->ws, ctx->queue, ctx->qkey, ctx->queue2, n, st);
+      if (timed && !r1) cudaEventRecord(ctx->ev[1], st);
+      r2 = r1 ? r1 : launch_stiff_phase<S>(ctx, b, n, st);
+    }
     if (timed && !r1 && !r2) cudaEventRecord(ctx->ev[2], st);
     if (r1 == -1 || r2 == -1) return CHEM_EUNSUPPORTED;
     if (r1 || r2) return cuda_fail(static_cast<cudaError_t>(r1 ? r1 : r2), "kernel launch");
@@ -367,13 +445,15 @@ void ctx_set_launch(chem_ctx* c, int bulk_grid, int stiff_grid) {
 void ctx_get_params(const chem_ctx* c, chem_params* p) { *p = c->prm; }
 int occupancy_bulk(const chem_ctx* c) {
   int b = 0;
-  if (bulk_occupancy(c->ns, false, c->blob_bytes, &b) != 0 || b < 1) b = 1;
-  return b;
+  const int r = c->large ? occupancy_lg(c->ns, c->nr, c->ntb, c->blob_bytes, false, &b)
+                         : bulk_occupancy(c->ns, false, c->blob_bytes, &b);
+  return (r != 0 || b < 1) ? 1 : b;
 }
 int occupancy_stiff(const chem_ctx* c) {
   int b = 0;
-  if (stiff_occupancy(c->ns, c->blob_bytes, &b) != 0 || b < 1) b = 1;
-  return b;
+  const int r = c->large ? occupancy_lg(c->ns, c->nr, c->ntb, c->blob_bytes, true, &b)
+                         : stiff_occupancy(c->ns, c->blob_bytes, &b);
+  return (r != 0 || b < 1) ? 1 : b;
 }
 // surrogate state and the mechanism data it needs (surrogate.cu)
 sg::State* ctx_surrogate(chem_ctx* c) { return c->sg; }
@@ -423,7 +503,8 @@ int chem_init(const chem_mechanism* mech, const chem_params* params, int64_t max
     prm = *params;
   }
   if (max_cells < 0 || max_cells > 0x7fffffffLL) return CHEM_EINVAL;
-  if (!compiled_ns(mech->ns)) return CHEM_EUNSUPPORTED;
+  const bool large = mech->ns > 15;
+  if (large ? !compiled_large(mech->ns) : !compiled_ns(mech->ns)) return CHEM_EUNSUPPORTED;
   chem_ctx* c = new (std::nothrow) chem_ctx();
   if (!c) return CHEM_ENOMEM;
   c->prm = prm;
@@ -433,17 +514,20 @@ int chem_init(const chem_mechanism* mech, const chem_params* params, int64_t max
   c->W.assign(mech->W, mech->W + mech->ns);
   c->nu_f.assign(mech->nu_f, mech->nu_f + static_cast<size_t>(mech->nr) * mech->ns);
   c->nu_r.assign(mech->nu_r, mech->nu_r + static_cast<size_t>(mech->nr) * mech->ns);
+  c->large = large;
   std::vector<unsigned char> blob;
-  pack_mechanism(mech, blob, &c->ntb);
-  c->blob_bytes = static_cast<unsigned>(blob.size());
   auto fail = [&](int code) {
     chem_destroy(c);
     return code;
   };
+  if ((rc = pack_mechanism(mech, blob, &c->ntb, large))) return fail(rc);
+  const unsigned blob_total = static_cast<unsigned>(blob.size());
+  // the staged part: the whole dense blob, or the large layout's prefix (its tail stays global)
+  c->blob_bytes = reinterpret_cast<const MechHdr*>(blob.data())->prefix;
   if ((rc = cuda_fail(cudaGetDevice(&c->dev), "cudaGetDevice"))) return fail(rc);
   if ((rc = cuda_fail(cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->dev), "attr"))) return fail(rc);
-  if (cudaMalloc(&c->blob, c->blob_bytes) != cudaSuccess) return fail(CHEM_ENOMEM);
-  if ((rc = cuda_fail(cudaMemcpy(c->blob, blob.data(), c->blob_bytes, cudaMemcpyHostToDevice), "copy mechanism")))
+  if (cudaMalloc(&c->blob, blob_total) != cudaSuccess) return fail(CHEM_ENOMEM);
+  if ((rc = cuda_fail(cudaMemcpy(c->blob, blob.data(), blob_total, cudaMemcpyHostToDevice), "copy mechanism")))
     return fail(rc);
   if (cudaMalloc(&c->ws, sizeof(Workspace)) != cudaSuccess) return fail(CHEM_ENOMEM);
   if (cudaMallocHost(&c->ws_host, sizeof(Workspace)) != cudaSuccess) return fail(CHEM_ENOMEM);
@@ -452,12 +536,8 @@ int chem_init(const chem_mechanism* mech, const chem_params* params, int64_t max
   if (cudaMalloc(&c->queue, sizeof(int) * qcap) != cudaSuccess) return fail(CHEM_ENOMEM);
   if (cudaMalloc(&c->queue2, sizeof(int) * qcap) != cudaSuccess) return fail(CHEM_ENOMEM);
   if (cudaMalloc(&c->qkey, qcap) != cudaSuccess) return fail(CHEM_ENOMEM);
-  int bpsm = 0;
-  if (bulk_occupancy(c->ns, false, c->blob_bytes, &bpsm) != 0 || bpsm < 1) bpsm = 1;
-  c->bulk_grid = c->sms * bpsm;
-  int spsm = 0;
-  if (stiff_occupancy(c->ns, c->blob_bytes, &spsm) != 0 || spsm < 1) spsm = 1;
-  c->stiff_grid = c->sms * spsm;
+  c->bulk_grid = c->sms * occupancy_bulk(c);
+  c->stiff_grid = c->sms * occupancy_stiff(c);
   for (auto& e : c->ev)
     if (cudaEventCreate(&e) != cudaSuccess) return fail(CHEM_ECUDA);
   if ((rc = ensure_two_pass(c))) return fail(rc);
@@ -621,9 +701,18 @@ int chem_advance_boxes(chem_ctx* ctx, void* stream) {
     if (order) b.queue = ctx->queue2;
     long long want = (n + kBulkBlock - 1) / kBulkBlock;
     const int bgrid = static_cast<int>(want < ctx->bulk_grid ? (want < 1 ? 1 : want) : ctx->bulk_grid);
-    int r1 = launch_bulk_f32(ctx->ns, a, bgrid, st);
-    if (!r1 && order) r1 = launch_order_queue(ctx->ws, ctx->queue, ctx->qkey, ctx->queue2, n, st);
-    int r2 = r1 ? r1 : launch_stiff_phase<float>(ctx, b, n, st);
+    int r1, r2;
+    if (ctx->large) {
+      const long long wb = (n + 7) / 8;
+      const int lgrid = static_cast<int>(wb < ctx->bulk_grid ? (wb < 1 ? 1 : wb) : ctx->bulk_grid);
+      r1 = launch_bulk_lg(ctx->ns, ctx->nr, ctx->ntb, a, lgrid, st);
+      if (!r1 && order) r1 = launch_order_queue(ctx->ws, ctx->queue, ctx->qkey, ctx->queue2, n, st);
+      r2 = r1 ? r1 : launch_stiff_lg(ctx->ns, ctx->nr, ctx->ntb, b, ctx->stiff_grid, st);
+    } else {
+      r1 = launch_bulk_f32(ctx->ns, a, bgrid, st);
+      if (!r1 && order) r1 = launch_order_queue(ctx->ws, ctx->queue, ctx->qkey, ctx->queue2, n, st);
+      r2 = r1 ? r1 : launch_stiff_phase<float>(ctx, b, n, st);
+    }
     if (r1 == -1 || r2 == -1) return CHEM_EUNSUPPORTED;
     if (r1 || r2) return cuda_fail(static_cast<cudaError_t>(r1 ? r1 : r2), "kernel launch");
   }
@@ -689,8 +778,10 @@ int chem_rates(chem_ctx* ctx, const float* rho, const float* T, const float* Y, 
                void* stream) {
   if (!ctx || n < 0 || (n > 0 && (!rho || !T || !Y || !dYdt || ld < n))) return CHEM_EINVAL;
   if (n == 0) return CHEM_OK;
-  const int r = launch_rates(ctx->ns, ctx->blob, ctx->blob_bytes, rho, T, Y, ld, n, dYdt, &ctx->ws->status,
-                             static_cast<cudaStream_t>(stream));
+  const int r = ctx->large ? launch_rates_lg(ctx->ns, ctx->nr, ctx->ntb, ctx->blob, ctx->blob_bytes, rho, T, Y, ld, n,
+                                             dYdt, &ctx->ws->status, static_cast<cudaStream_t>(stream))
+                           : launch_rates(ctx->ns, ctx->blob, ctx->blob_bytes, rho, T, Y, ld, n, dYdt,
+                                          &ctx->ws->status, static_cast<cudaStream_t>(stream));
   return r == -1 ? CHEM_EUNSUPPORTED : cuda_fail(static_cast<cudaError_t>(r), "rates kernel");
 }
 

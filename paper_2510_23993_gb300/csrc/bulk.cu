@@ -253,6 +253,9 @@ __global__ void __launch_bounds__(kBulkBlock) rates_kernel(const unsigned char* 
 // ------------------------------------------------------------------ launchers
 
 #define CHEM_FOR_EACH_NS(X) X(9)
+// species counts of the thread-per-cell thermo helpers (state_kernel, temperature_kernel): also
+// the large mechanisms, whose staged table prefix carries the same thermo layout
+#define CHEM_FOR_EACH_NS_THERMO(X) X(9) X(53)
 
 size_t bulk_smem_bytes(unsigned blob_bytes, int nbox) {
   return ((blob_bytes + 127u) & ~127u) + box_smem_bytes(nbox);
@@ -312,11 +315,12 @@ int launch_state_from_TpY_f32(int ns, const unsigned char* blob, unsigned bytes,
                               cudaStream_t s) {
 #define X(N)                                                                                           \
   if (ns == N) {                                                                                       \
+    cudaFuncSetAttribute(state_kernel<N, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);  \
     state_kernel<N, float><<<grid_for(n), kBulkBlock, bytes, s>>>(blob, bytes, T, p, Y, ld, n, rho, e, \
                                                                   status);                             \
     return static_cast<int>(cudaGetLastError());                                                       \
   }
-  CHEM_FOR_EACH_NS(X)
+  CHEM_FOR_EACH_NS_THERMO(X)
 #undef X
   return -1;
 }
@@ -326,11 +330,12 @@ int launch_state_from_TpY_f64(int ns, const unsigned char* blob, unsigned bytes,
                               cudaStream_t s) {
 #define X(N)                                                                                            \
   if (ns == N) {                                                                                        \
+    cudaFuncSetAttribute(state_kernel<N, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);  \
     state_kernel<N, double><<<grid_for(n), kBulkBlock, bytes, s>>>(blob, bytes, T, p, Y, ld, n, rho, e, \
                                                                    status);                             \
     return static_cast<int>(cudaGetLastError());                                                        \
   }
-  CHEM_FOR_EACH_NS(X)
+  CHEM_FOR_EACH_NS_THERMO(X)
 #undef X
   return -1;
 }
@@ -339,10 +344,11 @@ int launch_temperature(int ns, const unsigned char* blob, unsigned bytes, const 
                        const float* e, long long n, float* T, int* status, cudaStream_t s) {
 #define X(N)                                                                                       \
   if (ns == N) {                                                                                   \
+    cudaFuncSetAttribute(temperature_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);  \
     temperature_kernel<N><<<grid_for(n), kBulkBlock, bytes, s>>>(blob, bytes, Y, ld, e, n, T, status); \
     return static_cast<int>(cudaGetLastError());                                                   \
   }
-  CHEM_FOR_EACH_NS(X)
+  CHEM_FOR_EACH_NS_THERMO(X)
 #undef X
   return -1;
 }

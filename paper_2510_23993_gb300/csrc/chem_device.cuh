@@ -34,6 +34,11 @@ struct MechHdr {
   int off_eff, off_rinfo, off_W, off_invW;
   int off_gam, off_hco, off_hsp, off_e64;
   int off_arr64, off_gam64, off_eff64, bytes;
+  // large-mechanism layout (large != 0, large.cu): sparse stoichiometry instead of the dense
+  // rows, a species -> reaction index, and the thermo regimes below / above the fit range in a
+  // global-only tail after the `prefix` bytes that are staged into shared memory
+  int off_sto, off_cptr, off_cent, off_gamg;
+  int off_hcog, prefix, nnz, large;
 };
 
 // Device view of the (staged) tables.

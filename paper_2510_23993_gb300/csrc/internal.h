@@ -150,6 +150,15 @@ size_t bulk_smem_bytes(unsigned blob_bytes, int nbox);
 int stiff_occupancy(int ns, unsigned blob_bytes, int* blocks_per_sm);
 int bulk_occupancy(int ns, bool f64, unsigned blob_bytes, int* blocks_per_sm);
 
+// large mechanisms (large.cu): one warp per cell, sparse stoichiometry
+bool compiled_large(int ns);
+int launch_bulk_lg(int ns, int nr, int ntb, const AdvanceArgs<float>& a, int grid, cudaStream_t s);
+int launch_stiff_lg(int ns, int nr, int ntb, const AdvanceArgs<float>& a, int grid, cudaStream_t s);
+int launch_rates_lg(int ns, int nr, int ntb, const unsigned char* blob, unsigned bytes, const float* rho,
+                    const float* T, const float* Y, long long ld, long long n, float* dYdt, int* status,
+                    cudaStream_t s);
+int occupancy_lg(int ns, int nr, int ntb, unsigned prefix, bool stiff, int* blocks_per_sm);
+
 int launch_state_from_TpY_f32(int ns, const unsigned char* blob, unsigned blob_bytes, const float* T,
                               const float* p, const float* Y, long long ld, long long n, float* rho,
                               float* e, int* status, cudaStream_t s);
