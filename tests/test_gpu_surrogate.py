@@ -292,3 +292,54 @@ def test_trained_gate_accuracy_and_gain(h2mech):
     rej = ~g["acc"]
     assert np.array_equal(g["T"][rej], pl["T"][rej]) and np.array_equal(g["Y"][:, rej], pl["Y"][:, rej])
     ctx.close()
+
+
+def test_save_load_round_trip_and_gated_edge_cases(h2mech):
+    """A saved surrogate reloads bit for bit into another context; the gated step handles an
+    empty call, a padded leading dimension and invalid cells (never accepted, flagged by the
+    plain path)."""
+    X, Yt = _raw_batch(h2mech, 4096, seed=16)
+    blob, _ = _oracle_checkpoint(h2mech, X, Yt, seed=6)
+    T, p, Y, rho, e, hot = _sheet(h2mech, 10, seed=6)
+    n = T.size
+    a = chem.Context(h2mech, max_cells=n)
+    a.surrogate_load(blob)
+    saved = a.surrogate_save()
+    assert saved == blob
+    b = chem.Context(h2mech, max_cells=n)
+    b.surrogate_load(saved)
+    oa = torch.zeros((n, 11), dtype=torch.float32, device=DEV)
+    ob = torch.zeros_like(oa)
+    a.surrogate_infer(_dev(T), _dev(Y), _dev(rho), _dev(e), 1e-8, oa)
+    b.surrogate_infer(_dev(T), _dev(Y), _dev(rho), _dev(e), 1e-8, ob)
+    assert torch.equal(oa, ob)
+    # empty call
+    z = torch.zeros(0, dtype=torch.float32, device=DEV)
+    zY = torch.zeros((9, 0), dtype=torch.float32, device=DEV)
+    assert a.advance_gated(z, z, zY, z, z, 1e-8, 1e-5, torch.zeros(0, dtype=torch.uint8, device=DEV),
+                           torch.zeros(0, dtype=torch.int32, device=DEV)) == 0
+    # padded leading dimension and two invalid cells, against the same step with ld = n
+    ld = n + 37
+    Tb, Yb = T.copy(), Y.copy()
+    Tb[3] = np.nan
+    Yb[0, 7] = -0.5
+    tY = torch.full((9, ld), -3.0, dtype=torch.float32, device=DEV)
+    tY[:, :n] = torch.from_numpy(Yb).to(DEV)
+    acc = torch.zeros(n, dtype=torch.uint8, device=DEV)
+    sub = torch.zeros(n, dtype=torch.int32, device=DEV)
+    tT, tp = _dev(Tb), _dev(p)
+    chem.chem_advance_gated(a.handle, tT, tp, tY, ld, _dev(rho), _dev(e), n, 1e-8, 1e-5, acc, sub)
+    st = a.status()
+    assert np.all(tY[:, n:].cpu().numpy() == -3.0)
+    acc_h, sub_h = acc.cpu().numpy(), sub.cpu().numpy()
+    assert acc_h[3] == 0 and acc_h[7] == 0 and sub_h[3] == -1 and sub_h[7] == -1
+    assert st["ninvalid"] == 2
+    tY2 = torch.from_numpy(np.ascontiguousarray(Yb)).to(DEV)
+    acc2 = torch.zeros(n, dtype=torch.uint8, device=DEV)
+    sub2 = torch.zeros(n, dtype=torch.int32, device=DEV)
+    tT2, tp2 = _dev(Tb), _dev(p)
+    a.advance_gated(tT2, tp2, tY2, _dev(rho), _dev(e), 1e-8, 1e-5, acc2, sub2)
+    assert torch.equal(acc, acc2) and torch.equal(sub, sub2)
+    assert torch.equal(tY[:, :n], tY2) and torch.equal(torch.nan_to_num(tT), torch.nan_to_num(tT2))
+    a.close()
+    b.close()
