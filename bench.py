@@ -38,17 +38,24 @@ METRIC = "chem cell-steps/s at rel err ≤1e-4 (gated surrogate vs plain GPU), %
 UNIT = "cell-steps/s"
 DT = 1e-8
 N_EDGE = 128
-NS = 9
-# algorithmic FP64 flops of the stiff integrator per unit of work (n = 9 species):
+# algorithmic FP64 flops of the stiff integrator per unit of work (n species):
 #   per attempted step: iteration matrix I - g h J (2 n^2) + LU with partial pivoting
 #       (sum_k 2 (n-k-1)^2 + (n-k-1), plus n reciprocals) + error filter (5 n + 2 n^2 + 2 n)
 #   per Newton iteration: T(e) (mixture 12 n + 2 iterations x 21) + residual 3 n + solve 2 n^2
 #       + update/norm 2 n
 #   per accepted step: T(e) of the new state (12 n + 42)
-F_ATTEMPT = 2 * NS * NS + sum(2 * (NS - k - 1) ** 2 + (NS - k - 1) for k in range(NS)) + NS \
-    + 5 * NS + 2 * NS * NS + 2 * NS
-F_NEWTON = (12 * NS + 42) + 3 * NS + 2 * NS * NS + 2 * NS
-F_ACCEPT = 12 * NS + 42
+
+
+def f_attempt(n):
+    return 2 * n * n + sum(2 * (n - k - 1) ** 2 + (n - k - 1) for k in range(n)) + n + 5 * n + 2 * n * n + 2 * n
+
+
+def f_newton(n):
+    return (12 * n + 42) + 3 * n + 2 * n * n + 2 * n
+
+
+def f_accept(n):
+    return 12 * n + 42
 # FP64 peak derived from the unit count: 152 SMs x 2 FP64 FMA lanes/clock x 2 flops x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -57,6 +64,14 @@ CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.ac
 
 
 def _config(n, args):
+    if args.config == 4:
+        e = args.edge
+        return {"workload": f"reacting sheet {2 * e}x{2 * e}x{e} ({n} cells, 4% reacting), hydrocarbon-shaped "
+                            f"mechanism 53 species / 325 reactions (30 third-body), dt = {DT:g} s, FP32 state, "
+                            f"bulk-sparse, one warp per cell",
+                "cells": n, "dt_s": DT, "rtol": args.rtol, "atol": args.atol,
+                "l2": "flushed (256 MiB write) and state restored from a pristine copy inside every step",
+                "mechanism_seed": 0, "field_seed": "rank"}
     return {"workload": f"reacting sheet {args.edge}^3 ({n} cells, 5% reacting), H2-air-shaped mechanism "
                         f"9 species / 21 reactions, dt = {DT:g} s, FP32 state, bulk-sparse",
             "cells": n, "dt_s": DT, "rtol": args.rtol, "atol": args.atol,
@@ -64,7 +79,11 @@ def _config(n, args):
             "mechanism_seed": 0, "field_seed": "rank"}
 
 
-def _field(seed, edge=N_EDGE):
+def _field(seed, edge=N_EDGE, config=1):
+    if config == 4:   # 2e x 2e x e sheet, 4% reacting, 53-species mechanism (256 x 256 x 128 at e = 128)
+        mech = synth.hydrocarbon_mechanism(0)
+        T, p, Y, hot = synth.sheet_field(mech, nx=2 * edge, ny=2 * edge, nz=edge, frac=0.04, seed=seed)
+        return mech, T.astype(np.float32), p.astype(np.float32), np.ascontiguousarray(Y, dtype=np.float32), hot
     mech = synth.h2_air_mechanism(0)
     T, p, Y, hot = synth.sheet_field(mech, n=edge, seed=seed)
     return mech, T.astype(np.float32), p.astype(np.float32), np.ascontiguousarray(Y, dtype=np.float32), hot
@@ -121,8 +140,9 @@ def run_gpu(args, rank, world, local_rank, dist):
     chem.build()
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    mech, T, p, Y, hot = _field(seed=rank, edge=args.edge)
+    mech, T, p, Y, hot = _field(seed=rank, edge=args.edge, config=args.config)
     n = T.size
+    ns = mech["ns"]
     flags = chem.CHEM_FLAG_TIMING | chem.CHEM_FLAG_ORDER_RATE | (chem.CHEM_FLAG_FP64_RATES if args.fp64_rates else 0) \
         | (chem.CHEM_FLAG_TWO_PASS if args.two_pass else 0)
     ctx = chem.Context(mech, max_cells=max(n, args.train_pairs), rtol=args.rtol, atol=args.atol, flags=flags)
@@ -165,12 +185,13 @@ def run_gpu(args, rank, world, local_rank, dist):
     # dominant kernel: the stiff kernel (FP64 pipe); its algorithmic FP64 work per launch
     stiff_ms = float(np.mean([s["stiff_ms"] for s in stats]))
     bulk_ms = float(np.mean([s["bulk_ms"] for s in stats]))
-    flops = float(np.mean([s["attempts"] * F_ATTEMPT + s["newton"] * F_NEWTON + s["substeps"] * F_ACCEPT
+    flops = float(np.mean([s["attempts"] * f_attempt(ns) + s["newton"] * f_newton(ns) + s["substeps"] * f_accept(ns)
                            for s in stats]))
     achieved = flops / (stiff_ms / 1e3) / 1e12
     roof = {"kernel": "stiff_kernel", "bound": "alu", "pipe": "fp64", "achieved": achieved,
             "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-            "traffic": _traffic(), "kernel_ms": stiff_ms, "bulk_kernel_ms": bulk_ms,
+            "traffic": _traffic() if args.config == 1 and args.edge == N_EDGE else None,
+            "kernel_ms": stiff_ms, "bulk_kernel_ms": bulk_ms,
             "algorithmic_flops_per_launch": flops,
             "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2.07 GHz (no FP64 figure in MEASURED_PEAKS.json)"}
     # end to end through the host entry point (pinned host buffers, copies inside the timing)
@@ -190,7 +211,7 @@ def run_gpu(args, rank, world, local_rank, dist):
                 wall += time.perf_counter() - t0
         wall = max_over_ranks(wall, dist)
         e2e = {"value": total_cells * args.steps / wall, "unit": UNIT,
-               "h2d_bytes_per_step": int(n * 4 * (NS + 4)), "d2h_bytes_per_step": int(n * 4 * (NS + 3))}
+               "h2d_bytes_per_step": int(n * 4 * (ns + 4)), "d2h_bytes_per_step": int(n * 4 * (ns + 3))}
     # kernels per step: bulk, queue order, stiff (two-pass: + continuation order + second stiff launch)
     per_step = 5 if ctx.params.flags & chem.CHEM_FLAG_TWO_PASS else 3
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -201,16 +222,18 @@ def run_gpu(args, rank, world, local_rank, dist):
             "stiff": {"queued_cells": stats[-1]["nqueued"], "bulk_cells": stats[-1]["nbulk"],
                       "substeps_per_stiff_cell": stats[-1]["substeps"] / max(1, stats[-1]["nqueued"]),
                       "newton_per_attempt": stats[-1]["newton"] / max(1, stats[-1]["attempts"])}}
-    if args.gated:
+    if args.gated and ns == 9:   # the surrogate is compiled for the 9-species mechanism
         line["gated"] = _gated_leg(args, ctx, chem, torch, dev, mech, step_inputs=(tT, tp, tY, rho, e, sub, T0, Y0, flush),
                                    plain_ms=ms / args.steps, n=n, world=world, dist=dist, rank=rank)
     if rank == 0 and world == 1 and args.cpu_baseline:
-        idx, orho, oe, oT, oY, wall, cores = _oracle_sample(mech, T, p, Y, hot, args.cpu_sample, seed=0)
+        # the 53-species oracle costs ~15 s per stiff cell per core: a smaller sample for config 4
+        n_sample = args.cpu_sample if args.config == 1 else min(args.cpu_sample, 256)
+        idx, orho, oe, oT, oY, wall, cores = _oracle_sample(mech, T, p, Y, hot, n_sample, seed=0)
         line["cpu_baseline"] = {"value": len(idx) / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": f"{len(idx)} cells stratified from the same field "
                                           f"({int(hot[idx].sum())} reacting), FP64 Radau IIA rtol 1e-10"}
         line["accuracy"] = _accuracy(ctx, torch, dev, T[idx], p[idx], Y[:, idx], orho, oe, oT, oY)
-        if args.gated:
+        if "gated" in line:
             line["gated"]["accuracy"] = _accuracy(ctx, torch, dev, T[idx], p[idx], Y[:, idx], orho, oe, oT, oY,
                                                   gate_tol=args.gate_tol)
     return line
@@ -318,10 +341,12 @@ def _traffic():
 
 
 def run_reference(args, world):
-    mech, T, p, Y, hot = _field(seed=0, edge=args.edge)
+    mech, T, p, Y, hot = _field(seed=0, edge=args.edge, config=args.config)
     walls, ncell = [], 0
     for i in range(args.warmup + args.steps):
-        idx, _, _, _, _, wall, cores = _oracle_sample(mech, T, p, Y, hot, args.ref_sample, seed=i)
+        idx, _, _, _, _, wall, cores = _oracle_sample(mech, T, p, Y, hot,
+                                                      args.ref_sample if args.config == 1 else min(args.ref_sample, 256),
+                                                      seed=i)
         if i >= args.warmup:
             walls.append(wall)
             ncell += len(idx)
@@ -332,8 +357,9 @@ def run_reference(args, world):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": _config(T.size, args),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"{args.ref_sample} cells per step, stratified (5% reacting) from the "
-                                       f"{args.edge}^3 field; FP64 Radau IIA rtol 1e-10"},
+                             "sample": f"{ncell // max(1, args.steps)} cells per step, stratified "
+                                       f"({int(hot.mean() * 100 + 0.5)}% reacting) from the field of "
+                                       f"{T.size} cells; FP64 Radau IIA rtol 1e-10"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -344,6 +370,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--edge", type=int, default=N_EDGE, help="field edge (cells); 128 is the benchmark size")
+    ap.add_argument("--config", type=int, default=1, choices=[1, 4],
+                    help="1: 9-species sheet (the benchmark); 4: 53-species sheet of 2e x 2e x e cells")
     ap.add_argument("--rtol", type=float, default=1e-5)
     ap.add_argument("--atol", type=float, default=1e-10)
     ap.add_argument("--cpu-sample", type=int, default=8192)
