@@ -74,7 +74,8 @@ bool compiled_ns(int ns) { return ns == 9; }
 // Host-side packing of the mechanism into the device blob layout of chem_device.cuh.  The dense
 // layout (ns <= 15) holds full stoichiometric rows and FP64 copies of the rate tables; the large
 // layout (large.cu) holds packed sparse stoichiometry and a species -> reaction index instead, and
-// keeps the thermo regimes below / above the fit range in a tail that is not staged.
+// keeps the per-reaction Gibbs and enthalpy coefficients in a tail that is not staged (read
+// through L1), which leaves shared memory for more cells in flight.
 int pack_mechanism(const chem_mechanism* m, std::vector<unsigned char>& out, int* ntb_out, bool large = false) {
   const int ns = m->ns, nr = m->nr;
   const int nsp = (ns + 3) & ~3;
@@ -94,7 +95,7 @@ int pack_mechanism(const chem_mechanism* m, std::vector<unsigned char>& out, int
   h.T_lo = static_cast<float>(T_lo);
   h.T_hi = static_cast<float>(T_hi);
   h.lnP0R = static_cast<float>(std::log(kP0 / kR));
-  const int nreg = large ? 1 : 3;   // regimes of gam / hco in the staged part
+  const int nreg = large ? 0 : 3;   // regimes of gam / hco in the staged part (large: none, all global)
   unsigned off = align16(sizeof(MechHdr));
   h.off_arr = off; off = align16(off + 16u * nr);
   if (!large) {
@@ -224,9 +225,6 @@ int pack_mechanism(const chem_mechanism* m, std::vector<unsigned char>& out, int
     }
   }
   if (large) {
-    // regime-1 copies into the staged part
-    std::memcpy(F(h.off_gam), gam + nr * 8, 4u * nr * 8);
-    std::memcpy(F(h.off_hco), hco + nr * 8, 4u * nr * 8);
     // packed sparse stoichiometry: up to 3 (species, coefficient) pairs per side, 9 bits each
     int2* sto = reinterpret_cast<int2*>(out.data() + h.off_sto);
     for (int r = 0; r < nr; ++r) {

@@ -5,7 +5,8 @@
 // error test for every cell, compaction of the failures, SDIRK3 with simplified Newton on the
 // dense Jacobian and an FP64 LU for them), laid out for a warp:
 //   * the mechanism is sparse (<= 3 reactant and <= 3 product species per reaction, packed 9 bits
-//     each) with a species -> (reaction, dnu) index, so the tables (~60 KB) fit shared memory;
+//     each) with a species -> (reaction, dnu) index, so the staged tables take ~40 KB of shared
+//     memory (the per-reaction thermo coefficients stay in global memory, cached in L1);
 //   * a cell's state is spread over the lanes (species k on lane k mod 32); rates are computed
 //     lane-parallel over reactions into a per-warp array of rates of progress, then reduced per
 //     species over that species' reactions in a fixed order (deterministic, no atomics);
@@ -24,7 +25,7 @@
 namespace chem {
 namespace lg {
 
-constexpr int kStiffWarps = 4;   // cells in flight per CTA of the stiff kernel
+constexpr int kStiffWarps = 5;   // cells in flight per CTA of the stiff kernel (shared memory bound)
 constexpr int kBulkWarps = 8;    // cells in flight per CTA of the bulk kernel
 constexpr int kNewtMax = 6;
 constexpr double kNewtTol = 0.03;
@@ -48,8 +49,6 @@ struct LView {
   const float* W;
   const float* invW;
   const float* eff;     // [ntb][nsp]
-  const float* gam1;    // [nr][8] Gibbs coefficients, regime 1 (shared memory)
-  const float* hco1;    // [nr][8] enthalpy coefficients, regime 1
   const float* hsp;     // [3][ns][8] species h/RT coefficients
   const int2* sto;      // [nr] packed reactants, products
   const int* cptr;      // [ns + 1]
@@ -74,8 +73,6 @@ __device__ __forceinline__ LView make_lview(const unsigned char* sm, const unsig
   v.W = reinterpret_cast<const float*>(sm + h->off_W);
   v.invW = reinterpret_cast<const float*>(sm + h->off_invW);
   v.eff = reinterpret_cast<const float*>(sm + h->off_eff);
-  v.gam1 = reinterpret_cast<const float*>(sm + h->off_gam);
-  v.hco1 = reinterpret_cast<const float*>(sm + h->off_hco);
   v.hsp = reinterpret_cast<const float*>(sm + h->off_hsp);
   v.sto = reinterpret_cast<const int2*>(sm + h->off_sto);
   v.cptr = reinterpret_cast<const int*>(sm + h->off_cptr);
@@ -86,12 +83,9 @@ __device__ __forceinline__ LView make_lview(const unsigned char* sm, const unsig
   return v;
 }
 
-__device__ __forceinline__ const float* gam_of(const LView& m, int reg, int r) {
-  return reg == 1 ? m.gam1 + r * 8 : m.gamg + (reg * m.nr + r) * 8;
-}
-__device__ __forceinline__ const float* hco_of(const LView& m, int reg, int r) {
-  return reg == 1 ? m.hco1 + r * 8 : m.hcog + (reg * m.nr + r) * 8;
-}
+// per-reaction Gibbs / enthalpy coefficients (global, read through L1)
+__device__ __forceinline__ const float* gam_of(const LView& m, int reg, int r) { return m.gamg + (reg * m.nr + r) * 8; }
+__device__ __forceinline__ const float* hco_of(const LView& m, int reg, int r) { return m.hcog + (reg * m.nr + r) * 8; }
 
 // ---- per-warp scratch in shared memory
 struct ScratchLayout {
