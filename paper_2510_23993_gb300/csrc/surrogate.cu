@@ -16,7 +16,8 @@
 // dZ^T A with the batch split over CTAs) plus elementwise kernels (encoding, loss, GELU
 // derivative, bias gradients, optimiser).  Inference in chem_advance_gated is one fused
 // persistent kernel: all BF16 weights resident in shared memory, 128 cells per tile, the
-// activations of a tile kept in shared memory and TMEM between layers, followed by the gate:
+// activations of a tile kept in shared memory and TMEM between layers (eight warps: two per TMEM
+// lane quadrant, each converting half of the columns), followed by the gate:
 //   (i)   every feature inside its range over the training set (widened by 1e-3 of the range),
 //         and Y >= -atol,
 //   (ii)  predicted log10 error at most log10(gate_tol),
@@ -410,7 +411,9 @@ struct GatedArgs {
   float* out;                     // optional raw outputs [n][kNOut] (testing), or null
 };
 
-__global__ void __launch_bounds__(128, 1) surrogate_infer_kernel(const GatedArgs a) {
+constexpr int kInferThreads = 256;   // warps w and w + 4 share TMEM lanes 32 (w % 4).. and split the columns
+
+__global__ void __launch_bounds__(kInferThreads, 1) surrogate_infer_kernel(const GatedArgs a) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ uint64_t bar_s, bar_m, bar_mma;
   __shared__ uint32_t s_taddr;
@@ -424,14 +427,17 @@ __global__ void __launch_bounds__(128, 1) surrogate_infer_kernel(const GatedArgs
   const MechView m = make_view(sM);
   const Norm& nm = *reinterpret_cast<const Norm*>(sS + bNorm);
   const float* bias = reinterpret_cast<const float*>(sS + bBias);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, t = threadIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int t = threadIdx.x & (kH - 1);   // tile row of this thread (TMEM lane)
+  const bool rowner = threadIdx.x < kH;   // threads 0..127 own the rows (features, outputs, gate)
+  const int col0 = (warp >> 2) * (kH / 2); // epilogue columns of this warp: [col0, col0 + 64)
   if (warp == 0) tc::tmem_alloc(&s_taddr, 128);
-  if (t == 0) tc::mbar_init(&bar_mma, 1);
+  if (threadIdx.x == 0) tc::mbar_init(&bar_mma, 1);
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t taddr = s_taddr;
-  const uint32_t lane_addr = taddr + (static_cast<uint32_t>(warp * 32) << 16);
+  const uint32_t lane_addr = taddr + (static_cast<uint32_t>((warp & 3) * 32) << 16);
   uint32_t phase = 0;
   bool ok = true;
   unsigned long long c_acc = 0;
@@ -439,7 +445,7 @@ __global__ void __launch_bounds__(128, 1) surrogate_infer_kernel(const GatedArgs
   const long long ntiles = (a.n + kH - 1) / kH;
   for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
     const long long i = tile * kH + t;
-    const bool valid = i < a.n;
+    const bool valid = rowner && i < a.n;
     float y[kNS], T = 0.0f, rho = 1.0f, e = 0.0f;
     float x[kNIn];
     bool inbox = valid;
@@ -468,7 +474,7 @@ __global__ void __launch_bounds__(128, 1) surrogate_infer_kernel(const GatedArgs
       for (int j = 0; j < kNIn; ++j) x[j] = nm.mu_x[j];
     }
     // standardised features -> BF16 row t of the X tile
-    {
+    if (rowner) {
       uint32_t w[8];
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
@@ -487,7 +493,7 @@ __global__ void __launch_bounds__(128, 1) surrogate_infer_kernel(const GatedArgs
       tc::fence_async_smem();
       tc::fence_before_sync();
       __syncthreads();
-      if (t == 0) {
+      if (threadIdx.x == 0) {
         tc::fence_after_sync();
         const int K = layer == 0 ? kKIn : kH;
         const int N = layer == 4 ? kNOutPad : kH;
@@ -508,7 +514,7 @@ __global__ void __launch_bounds__(128, 1) surrogate_infer_kernel(const GatedArgs
       tc::fence_after_sync();
       if (layer < 4) {
         const float* bl = bias + layer * kH;
-        for (int n0 = 0; n0 < kH; n0 += 16) {
+        for (int n0 = col0; n0 < col0 + kH / 2; n0 += 16) {
           float v[16];
           tc::tmem_ld16(lane_addr + n0, v);
           uint32_t w[8];
@@ -521,7 +527,7 @@ __global__ void __launch_bounds__(128, 1) surrogate_infer_kernel(const GatedArgs
           *reinterpret_cast<uint4*>(sHt + tc::kmajor_offset(t, n0, kH)) = make_uint4(w[0], w[1], w[2], w[3]);
           *reinterpret_cast<uint4*>(sHt + tc::kmajor_offset(t, n0 + 8, kH)) = make_uint4(w[4], w[5], w[6], w[7]);
         }
-      } else {
+      } else if (rowner) {
         tc::tmem_ld16(lane_addr, o);
 #pragma unroll
         for (int j = 0; j < kNOutPad; ++j) o[j] += bias[4 * kH + j];
@@ -569,7 +575,7 @@ __global__ void __launch_bounds__(128, 1) surrogate_infer_kernel(const GatedArgs
   if (!ok) {
     // an MMA did not signal completion in time: record it and give it a second bounded chance
     // to finish before the accumulator is freed (phase was flipped past the missed completion)
-    if (t == 0) atomicOr(a.status, 32);
+    if (threadIdx.x == 0) atomicOr(a.status, 32);
     tc::mbar_wait(&bar_mma, phase ^ 1u);
   }
   // every thread waited for the last commit of the tiles it ran; free the accumulator
@@ -849,7 +855,7 @@ int launch_infer(chem_ctx* ctx, State* s, const GatedArgs& g0, cudaStream_t st) 
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const long long tiles = (g.n + kH - 1) / kH;
   const int grid = static_cast<int>(tiles < sms ? tiles : sms);
-  surrogate_infer_kernel<<<grid, 128, smem, st>>>(g);
+  surrogate_infer_kernel<<<grid, kInferThreads, smem, st>>>(g);
   return fail_cuda(cudaGetLastError(), "surrogate kernel");
 }
 
