@@ -64,6 +64,13 @@ CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.ac
 
 
 def _config(n, args):
+    if args.config == 3:
+        return {"workload": f"flat batch of {n} cells drawn from the AMR shear-layer state distribution (400 boxes "
+                            f"over 3 levels per draw, ~3% stiff), H2-air-shaped mechanism 9 species / 21 reactions, "
+                            f"dt = {DT:g} s, FP32 state; plain bulk-sparse vs gated surrogate",
+                "cells": n, "dt_s": DT, "rtol": args.rtol, "atol": args.atol,
+                "l2": "flushed (256 MiB write) and state restored from a pristine copy inside every step",
+                "mechanism_seed": 0, "field_seed": "rank"}
     if args.config == 4:
         e = args.edge
         return {"workload": f"reacting sheet {2 * e}x{2 * e}x{e} ({n} cells, 4% reacting), hydrocarbon-shaped "
@@ -79,7 +86,20 @@ def _config(n, args):
             "mechanism_seed": 0, "field_seed": "rank"}
 
 
-def _field(seed, edge=N_EDGE, config=1):
+def _field(seed, edge=N_EDGE, config=1, cells=16_000_000):
+    if config == 3:   # flat batch of cells drawn from the AMR jet-in-crossflow-like state distribution
+        mech = synth.h2_air_mechanism(0)
+        Ts, ps, Ys, hs = [], [], [], []
+        k = 0
+        while sum(t.size for t in Ts) < cells:
+            boxes = synth.amr_boxes(seed=2 * seed + k)
+            for T, p, Y, hot in synth.helix_box_fields(mech, boxes, seed=2 * seed + k, stiff_frac=0.03):
+                Ts.append(T), ps.append(p), Ys.append(Y), hs.append(hot)
+            k += 1
+        perm = np.random.default_rng(seed).permutation(sum(t.size for t in Ts))[:cells]
+        T, p, hot = np.concatenate(Ts)[perm], np.concatenate(ps)[perm], np.concatenate(hs)[perm]
+        Y = np.concatenate(Ys, axis=1)[:, perm]
+        return mech, T.astype(np.float32), p.astype(np.float32), np.ascontiguousarray(Y, dtype=np.float32), hot
     if config == 4:   # 2e x 2e x e sheet, 4% reacting, 53-species mechanism (256 x 256 x 128 at e = 128)
         mech = synth.hydrocarbon_mechanism(0)
         T, p, Y, hot = synth.sheet_field(mech, nx=2 * edge, ny=2 * edge, nz=edge, frac=0.04, seed=seed)
@@ -140,7 +160,7 @@ def run_gpu(args, rank, world, local_rank, dist):
     chem.build()
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    mech, T, p, Y, hot = _field(seed=rank, edge=args.edge, config=args.config)
+    mech, T, p, Y, hot = _field(seed=rank, edge=args.edge, config=args.config, cells=args.cells)
     n = T.size
     ns = mech["ns"]
     flags = chem.CHEM_FLAG_TIMING | chem.CHEM_FLAG_ORDER_RATE | (chem.CHEM_FLAG_FP64_RATES if args.fp64_rates else 0) \
@@ -247,7 +267,7 @@ def _gated_leg(args, ctx, chem, torch, dev, mech, step_inputs, plain_ms, n, worl
     tT, tp, tY, rho, e, sub, T0, Y0, flush = step_inputs
     nbox = 256
     m = args.train_pairs // nbox
-    Ts, ps, Ys, dts = synth.surrogate_samples(mech, nbox * m, seed=1000 + rank, premix_frac=0.5)
+    Ts, ps, Ys, dts = synth.surrogate_samples(mech, nbox * m, seed=1000 + rank, premix_frac=1 / 3, mixing_frac=1 / 3)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     X, Yt, keep = surrogate.make_pairs(ctx, torch.from_numpy(Ts.astype(np.float32)).to(dev),
@@ -293,9 +313,10 @@ def _gated_leg(args, ctx, chem, torch, dev, mech, step_inputs, plain_ms, n, worl
             "train": {"pairs": int(keep.sum().item()), "pairs_s": t_pairs, "epochs": args.train_epochs,
                       "train_s": t_train, "loss_first": losses[0] if losses else None,
                       "loss_last": losses[-1] if losses else None,
-                      "distribution": "T U[300,3200] K, p U[1,50] atm, Y Dirichlet(0.5) or premix-centred "
-                                      "Dirichlet (half each), dt log-U[1e-9,1e-6] s; targets by the plain "
-                                      "integrator at rtol 1e-6 / atol 1e-11 with FP64 rates"}}
+                      "distribution": "T U[300,3200] K, p U[1,50] atm, Y from Dirichlet(0.5), a premix-centred "
+                                      "Dirichlet or a fuel/air mixing-line Dirichlet (a third each), dt "
+                                      "log-U[1e-9,1e-6] s; targets by the plain integrator at rtol 1e-6 / atol "
+                                      "1e-11 with FP64 rates"}}
 
 
 def _accuracy(ctx, torch, dev, T, p, Y, rho, e, T_ref, Y_ref, gate_tol=None):
@@ -341,7 +362,7 @@ def _traffic():
 
 
 def run_reference(args, world):
-    mech, T, p, Y, hot = _field(seed=0, edge=args.edge, config=args.config)
+    mech, T, p, Y, hot = _field(seed=0, edge=args.edge, config=args.config, cells=args.cells)
     walls, ncell = [], 0
     for i in range(args.warmup + args.steps):
         idx, _, _, _, _, wall, cores = _oracle_sample(mech, T, p, Y, hot,
@@ -370,8 +391,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--edge", type=int, default=N_EDGE, help="field edge (cells); 128 is the benchmark size")
-    ap.add_argument("--config", type=int, default=1, choices=[1, 4],
-                    help="1: 9-species sheet (the benchmark); 4: 53-species sheet of 2e x 2e x e cells")
+    ap.add_argument("--config", type=int, default=1, choices=[1, 3, 4],
+                    help="1: 9-species sheet (the benchmark); 3: flat batch from the AMR state distribution "
+                         "(--cells), plain vs gated; 4: 53-species sheet of 2e x 2e x e cells")
+    ap.add_argument("--cells", type=int, default=16_000_000, help="cells of the --config 3 batch")
     ap.add_argument("--rtol", type=float, default=1e-5)
     ap.add_argument("--atol", type=float, default=1e-10)
     ap.add_argument("--cpu-sample", type=int, default=8192)

@@ -396,6 +396,10 @@ class Context:
         cp = cache_path.encode() if cache_path else None
         _check(lib().chem_tune(self.handle, _dp(T), _dp(p), _dp(Y), Y.stride(0), _dp(rho), _dp(e), T.shape[0],
                                float(dt), _dp(substeps), cp, ctypes.byref(res), _stream(stream)), "chem_tune")
+        # keep the parameter mirror in step with what the tuner applied
+        order_bits = CHEM_FLAG_ORDER_RATE | CHEM_FLAG_ORDER_PREV | CHEM_FLAG_TWO_PASS
+        self.params.k_bulk = res.k_bulk
+        self.params.flags = (self.params.flags & ~order_bits) | res.flags
         return res.as_dict()
 
     def set_boxes(self, boxes):

@@ -162,19 +162,40 @@ def helix_box_fields(mech, boxes, seed=0, stiff_frac=0.03, alpha=0.5):
 
 
 def surrogate_samples(mech, n, seed=0, alpha=0.5, T_range=(300.0, 3200.0), p_atm=(1.0, 50.0),
-                      log_dt=(np.log(1e-9), np.log(1e-6)), premix_frac=0.0, kappa=200.0, alpha_trace=1e-3):
+                      log_dt=(np.log(1e-9), np.log(1e-6)), premix_frac=0.0, kappa=200.0, alpha_trace=1e-3,
+                      mixing_frac=0.0):
     """Inputs of surrogate training samples: T, p, Y ~ Dirichlet, dt log-uniform.
 
     A fraction `premix_frac` of the samples draws Y from a Dirichlet concentrated on the
     stoichiometric premix (concentrations kappa * Y_premix + alpha_trace): near-premix states with
-    trace radicals, the cold part of the reacting-front fields; the rest from Dirichlet(alpha)."""
+    trace radicals, the cold part of the reacting-front fields.  A fraction `mixing_frac` draws Y
+    from a Dirichlet concentrated on the fuel / air mixing line, Z Y_fuel + (1 - Z) Y_air with
+    Z ~ U[0, 1] and each end (pure fuel, pure air) taken exactly for a tenth of them: the cold part
+    of the shear-layer fields.  The rest draws from Dirichlet(alpha)."""
     rng = np.random.default_rng(seed + 15485863)
     T = rng.uniform(*T_range, size=n)
     p = rng.uniform(*p_atm, size=n) * P_ATM
     Y = rng.dirichlet(np.full(mech["ns"], alpha), size=n).T
     dt = np.exp(rng.uniform(*log_dt, size=n))
+    u = rng.random(n)
     if premix_frac > 0:
-        pick = rng.random(n) < premix_frac
+        pick = u < premix_frac
         conc = kappa * premix_mass_fractions(mech) + alpha_trace
         Y[:, pick] = rng.dirichlet(conc, size=int(pick.sum())).T
+    if mixing_frac > 0:
+        pick = np.nonzero((u >= premix_frac) & (u < premix_frac + mixing_frac))[0]
+        air = np.zeros(mech["ns"])
+        air[mech["oxidizer"]], air[mech["inert"]] = 1.0, 3.76
+        air *= mech["W"]
+        air /= air.sum()
+        fuel = np.zeros(mech["ns"])
+        fuel[mech["fuel"]] = 1.0
+        Z = rng.uniform(0.0, 1.0, size=pick.size)
+        end = rng.random(pick.size)
+        Z[end < 0.1], Z[(end >= 0.1) & (end < 0.2)] = 0.0, 1.0
+        base = Z[None, :] * fuel[:, None] + (1 - Z[None, :]) * air[:, None]
+        exact = (Z == 0.0) | (Z == 1.0)
+        draw = np.array([rng.dirichlet(kappa * base[:, j] + alpha_trace) for j in range(pick.size)]).T \
+            if pick.size else np.zeros((mech["ns"], 0))
+        Y[:, pick] = np.where(exact[None, :], base, draw)
     return T, p, Y, dt
