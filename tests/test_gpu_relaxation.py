@@ -1,0 +1,75 @@
+"""Analogue of the paper's verification (App. A) on the synthetic mechanism, with the FP64 oracle
+as the reference instead of Cantera (GPU).
+
+The paper compares ignition-delay curves of stoichiometric H2-air at 1 atm over 1500-2500 K.  The
+synthetic H2-air-shaped mechanism does not run away thermally at these states: the premix relaxes
+towards a radical-rich state and cools.  The observable is therefore the whole temperature history
+T(t) over five decades of time (1e-9 .. 1e-4 s, 51 log-spaced steps of chem_advance, each a full
+bulk-sparse call) and the characteristic time at which T has covered half of its final change,
+for five initial temperatures; both must match the oracle integrated over the same steps.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle
+import paper_2510_23993_gb300 as chem
+import synth
+
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    chem.build()
+
+
+def _half_time(grid, Ts, T0):
+    """First time at which |T - T0| reaches half of |T_end - T0| (log-linear interpolation)."""
+    target = 0.5 * abs(Ts[-1] - T0)
+    d = np.abs(Ts - T0)
+    k = int(np.argmax(d >= target))
+    t0, t1 = grid[max(k - 1, 1)], grid[k]
+    d0, d1 = d[k - 1], d[k]
+    w = (target - d0) / (d1 - d0) if d1 > d0 else 1.0
+    return float(np.exp(np.log(t0) + w * (np.log(t1) - np.log(t0))))
+
+
+def test_relaxation_histories_match_oracle(h2mech):
+    T0 = np.array([1500.0, 1750.0, 2000.0, 2250.0, 2500.0])
+    Y0 = np.repeat(synth.premix_mass_fractions(h2mech)[:, None], 5, axis=1)
+    p0 = np.full(5, synth.P_ATM)
+    T32, p32, Y32 = T0.astype(np.float32), p0.astype(np.float32), np.ascontiguousarray(Y0, dtype=np.float32)
+    rho, e = oracle.state_from_TpY(h2mech, T32, p32, Y32)
+    rho, e = rho.astype(np.float32), e.astype(np.float32)
+    grid = np.concatenate([[0.0], np.logspace(-9, -4, 51)])
+    # oracle
+    T, Y = T32.astype(np.float64), Y32.astype(np.float64)
+    T_ref = [T.copy()]
+    for a, b in zip(grid[:-1], grid[1:]):
+        T, _, Y, _ = oracle.advance(h2mech, rho, e, T, Y, b - a)
+        T_ref.append(T.copy())
+    T_ref = np.array(T_ref)
+    # GPU: the same steps, rtol 1e-6
+    ctx = chem.Context(h2mech, max_cells=5, rtol=1e-6)
+    tT, tp, tY, trho, te = (torch.from_numpy(np.ascontiguousarray(a)).to(DEV) for a in (T32, p32, Y32, rho, e))
+    sub = torch.zeros(5, dtype=torch.int32, device=DEV)
+    T_gpu = [T32.astype(np.float64)]
+    for a, b in zip(grid[:-1], grid[1:]):
+        ctx.advance(tT, tp, tY, trho, te, b - a, sub)
+        st = ctx.status()
+        assert st["status"] == 0
+        T_gpu.append(tT.cpu().numpy().astype(np.float64))
+    T_gpu = np.array(T_gpu)
+    # every point of the five histories, and the characteristic times
+    assert np.all(np.abs(T_gpu - T_ref) / T_ref <= 2e-4), np.abs(T_gpu - T_ref).max()
+    assert np.all(np.abs(T_ref[-1] - T0) > 10.0)   # a real relaxation happened (14 to 880 K)
+    for j in range(5):
+        th_ref = _half_time(grid, T_ref[:, j], T0[j])
+        th_gpu = _half_time(grid, T_gpu[:, j], T0[j])
+        assert abs(th_gpu - th_ref) <= 0.01 * th_ref, (T0[j], th_gpu, th_ref)
+    ctx.close()
