@@ -140,6 +140,23 @@ def advance(mech, rho, e, T, Y, dt, rtol=1e-10, atol=1e-14, T_min=0.0, max_steps
     return T, p, Y, steps
 
 
+def explicit(mech, rho, e, T, Y, dt, frac=0.05, y_floor=1e-10, T_min=0.0, k_max=100000):
+    """The paper's explicit first-order scheme (Sec. 2.1) per cell: forward Euler substeps that
+    change no Y_k by more than frac * max(|Y_k|, y_floor).  Returns (T, p, Y, steps); steps = 0
+    for cells below T_min, -1 for cells that do not reach dt within k_max substeps."""
+    lib, M = _load(), _Mech(mech)
+    rho, e = _f64(rho), _f64(e)
+    T = np.array(T, dtype=np.float64, copy=True)
+    Y = np.array(Y, dtype=np.float64, copy=True, order="C")
+    n = T.shape[0]
+    p = np.full(n, np.nan)
+    steps = np.zeros(n, dtype=np.int64)
+    lib.oracle_explicit(*M.args(), ctypes.c_int64(n), _p(rho, D), _p(e, D), _p(T, D), _p(p, D), _p(Y, D),
+                        ctypes.c_int64(n), ctypes.c_double(dt), ctypes.c_double(frac), ctypes.c_double(y_floor),
+                        ctypes.c_double(T_min), ctypes.c_int64(k_max), _p(steps, ctypes.c_int64))
+    return T, p, Y, steps
+
+
 def backward_euler(mech, rho, e, T, Y, dt, nsteps):
     """Brute force: nsteps uniform backward-Euler steps of one cell (Newton to round-off)."""
     lib, M = _load(), _Mech(mech)

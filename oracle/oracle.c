@@ -535,6 +535,49 @@ int oracle_temperature_ode(MECH_ARGS, double rho, double *Y, double *T, double d
   return 1;
 }
 
+/* The paper's own explicit scheme (Sec. 2.1; the per-cell loop of Algorithm 2, which Algorithm 3
+ * runs in pieces without changing any cell's sequence of substeps): forward Euler on Eq. 5 with
+ * each substep as long as keeps every |dY_k| within frac * max(|Y_k|, y_floor) and never past dt,
+ * T from e after every substep.  Cells with T < T_min are untouched (steps 0); steps = -1 when
+ * k_max substeps do not reach dt or T(e) fails (the state reached is kept). */
+void oracle_explicit(MECH_ARGS, int64_t n, const double *rho, const double *e, double *T, double *p,
+                     double *Y, int64_t ld, double dt, double frac, double y_floor, double T_min,
+                     int64_t k_max, int64_t *steps) {
+  omech m = make_mech(MECH_PASS);
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t i = 0; i < n; ++i) {
+    if (!(T[i] >= T_min)) { steps[i] = 0; continue; }
+    double y[MAXN], S[MAXN], om[MAXN];
+    for (int k = 0; k < ns; ++k) y[k] = Y[k * ld + i];
+    int ok;
+    double Ti = o_T_from_e(&m, y, e[i], T[i], &ok);
+    double t = 0.0;
+    int64_t K = 0;
+    while (ok && t < dt && K < k_max) {
+      o_rates(&m, rho[i], Ti, y, NULL, NULL, om);
+      const double rem = dt - t;
+      double h = rem;
+      for (int k = 0; k < ns; ++k) {
+        S[k] = W[k] * om[k] / rho[i];
+        if (S[k] != 0.0) h = fmin(h, frac * fmax(fabs(y[k]), y_floor) / fabs(S[k]));
+      }
+      double y1[MAXN];
+      for (int k = 0; k < ns; ++k) y1[k] = y[k] + h * S[k];
+      double T1 = o_T_from_e(&m, y1, e[i], Ti, &ok);
+      if (!ok) break;
+      memcpy(y, y1, sizeof(double) * ns);
+      Ti = T1;
+      t = h >= rem ? dt : t + h;
+      ++K;
+    }
+    steps[i] = (ok && t >= dt) ? K : -1;
+    double sw = 0.0;
+    for (int k = 0; k < ns; ++k) { Y[k * ld + i] = y[k]; sw += y[k] / W[k]; }
+    T[i] = Ti;
+    if (p) p[i] = rho[i] * R_GAS * Ti * sw;
+  }
+}
+
 int oracle_max_threads(void) {
 #ifdef _OPENMP
   return omp_get_max_threads();
