@@ -12,6 +12,9 @@ pristine device copy, flushes L2 (256 MiB write) and advances every cell through
 A second leg ("gated" in the JSON line) times the same steps with the learned surrogate in
 front of the method (chem_advance_gated), after training it on pairs made by the plain integrator
 (outside the timed region), and reports the accepted fraction and the sampled error vs the oracle.
+A third leg ("paper_loop") times the paper's own method on the same steps: explicit first-order
+substeps under the relative-change rule of Sec. 2.1, driven by Algorithm 3 (chem_advance_explicit),
+with its sampled error vs the oracle.
 
 Under torchrun (N > 1) every rank advances its own field (seed = rank): weak scaling, no
 collective on the data path; the step time is the max over ranks.  `--impl reference` times the
@@ -245,6 +248,9 @@ def run_gpu(args, rank, world, local_rank, dist):
     if args.gated and ns == 9:   # the surrogate is compiled for the 9-species mechanism
         line["gated"] = _gated_leg(args, ctx, chem, torch, dev, mech, step_inputs=(tT, tp, tY, rho, e, sub, T0, Y0, flush),
                                    plain_ms=ms / args.steps, n=n, world=world, dist=dist, rank=rank)
+    if args.paper_loop and ns == 9:   # the paper's explicit scheme is compiled for the dense path
+        line["paper_loop"] = _paper_loop_leg(args, ctx, chem, torch, step_inputs=(tT, tp, tY, rho, e, sub, T0, Y0, flush),
+                                             plain_ms=ms / args.steps, n=n, world=world, dist=dist)
     if rank == 0 and world == 1 and args.cpu_baseline:
         # the 53-species oracle costs ~15 s per stiff cell per core: a smaller sample for config 4
         n_sample = args.cpu_sample if args.config == 1 else min(args.cpu_sample, 256)
@@ -256,6 +262,12 @@ def run_gpu(args, rank, world, local_rank, dist):
         if "gated" in line:
             line["gated"]["accuracy"] = _accuracy(ctx, torch, dev, T[idx], p[idx], Y[:, idx], orho, oe, oT, oY,
                                                   gate_tol=args.gate_tol)
+        if "paper_loop" in line:
+            plain_frac = ctx.params.bulk_frac
+            ctx.set_params(bulk_frac=args.paper_frac)
+            line["paper_loop"]["accuracy"] = _accuracy(ctx, torch, dev, T[idx], p[idx], Y[:, idx], orho, oe, oT, oY,
+                                                       explicit=True)
+            ctx.set_params(bulk_frac=plain_frac)
     return line
 
 
@@ -319,14 +331,59 @@ def _gated_leg(args, ctx, chem, torch, dev, mech, step_inputs, plain_ms, n, worl
                                       "1e-11 with FP64 rates"}}
 
 
-def _accuracy(ctx, torch, dev, T, p, Y, rho, e, T_ref, Y_ref, gate_tol=None):
-    """Error of the GPU path (plain, or gated when gate_tol is given) against the oracle on the
-    CPU-baseline sample (oracle inputs)."""
+def _paper_loop_leg(args, ctx, chem, torch, step_inputs, plain_ms, n, world, dist):
+    """The same steps with the paper's own method (chem_advance_explicit): explicit first-order
+    substeps under the bulk_frac change rule (Sec. 2.1), bulk launches of 5 substeps while more
+    than 1e4 cells are active, then one sparse launch (Algorithm 3).  The host reads the active
+    count after every launch, as the paper does, so the step includes those synchronizations."""
+    tT, tp, tY, rho, e, sub, T0, Y0, flush = step_inputs
+    plain_frac = ctx.params.bulk_frac
+    ctx.set_params(bulk_frac=args.paper_frac)
+    launches = []
+
+    def pstep(i):
+        tT.copy_(T0)
+        tY.copy_(Y0)
+        flush.fill_(i & 0xFF)
+        launches.append(ctx.advance_explicit(tT, tp, tY, rho, e, DT, sub, k_steps=5, n_star=10000))
+        return ctx.status()
+
+    for i in range(args.warmup):
+        pstep(i)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches.clear()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    stats = [pstep(i) for i in range(args.steps)]
+    ev1.record()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    ms = max_over_ranks(ev0.elapsed_time(ev1), dist)
+    ctx.set_params(bulk_frac=plain_frac)
+    st = stats[-1]
+    return {"method": "explicit first-order substeps, |dY_k| <= frac max(|Y_k|, y_floor) (Sec. 2.1), Algorithm 3 "
+                      "control: bulk launches of K = 5 substeps while N_active > N* = 1e4, then one sparse launch "
+                      "(k_max 1e5)",
+            "frac": args.paper_frac, "value": n * world * args.steps / (ms / 1e3), "unit": UNIT,
+            "ms_per_step": ms / args.steps, "vs_plain": plain_ms / (ms / args.steps),
+            "bulk_launches": launches[-1], "sparse_cells": st["nqueued"], "failed_cells": st["nfailed"],
+            "explicit_substeps": st["substeps"],
+            "gpu_launches": sum(2 + nl for nl in launches) * world}
+
+
+def _accuracy(ctx, torch, dev, T, p, Y, rho, e, T_ref, Y_ref, gate_tol=None, explicit=False):
+    """Error of the GPU path (plain, gated when gate_tol is given, or the paper's explicit loop)
+    against the oracle on the CPU-baseline sample (oracle inputs)."""
     n = T.size
     a = [torch.from_numpy(np.ascontiguousarray(x)).to(dev) for x in (T, p, Y, rho, e)]
     s = torch.zeros(n, dtype=torch.int32, device=dev)
     nacc = None
-    if gate_tol is None:
+    if explicit:
+        ctx.advance_explicit(a[0], a[1], a[2], a[3], a[4], DT, s)
+    elif gate_tol is None:
         ctx.advance(a[0], a[1], a[2], a[3], a[4], DT, s)
     else:
         acc = torch.zeros(n, dtype=torch.uint8, device=dev)
@@ -408,6 +465,9 @@ def main():
                                                               "chooses it otherwise)")
     ap.add_argument("--no-gated", dest="gated", action="store_false", help="skip the gated-surrogate leg")
     ap.add_argument("--gate-tol", type=float, default=1e-5)
+    ap.add_argument("--no-paper-loop", dest="paper_loop", action="store_false",
+                    help="skip the leg that times the paper's explicit scheme under Algorithm 3")
+    ap.add_argument("--paper-frac", type=float, default=0.05, help="relative change limit of the explicit scheme")
     ap.add_argument("--train-pairs", type=int, default=262144)
     ap.add_argument("--train-epochs", type=int, default=40)
     args = ap.parse_args()

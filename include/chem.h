@@ -153,6 +153,32 @@ int chem_advance_f64(chem_ctx *ctx, double *T, double *p, double *Y, int64_t ld,
 int chem_advance_host(chem_ctx *ctx, float *T, float *p, float *Y, const float *rho,
                       const float *e, int64_t n, double dt, int32_t *substeps, void *stream);
 
+/* The paper's own integration method, kept as the comparison point of chem_advance: the explicit
+ * first-order adaptive scheme of Sec. 2.1 (Algorithm 2's per-cell loop: each substep as long as
+ * keeps every |dY_k| within params.bulk_frac * max(|Y_k|, params.y_floor), the "1-5%" rule, and
+ * never past dt; T from e by the FP64 inversion after every substep) under the bulk / sparse
+ * control of Algorithm 3:
+ *   section 1: one launch over all cells sets each cell's time to 0 (active) or dt (T < T_min,
+ *              invalid), solves its temperature from e and counts the active cells;
+ *   section 2: while the active count, copied to the host after every launch, exceeds n_star
+ *              (the paper's N* = 1e4), one launch over all cells in which each active cell takes
+ *              at most k_steps substeps (the paper's bulk K_max = 5);
+ *   section 3: one launch over the compacted list of the remaining active cells, each taking at
+ *              most params.k_max substeps (the paper's 1e5).
+ * The bulk phase ends after ceil(k_max / k_steps) launches even if more than n_star cells are
+ * still active (a bound the paper does not state).  Device pointers, FP32 state, same layout as
+ * chem_advance.  substeps[n] out: 0 skipped, the number of explicit substeps, or -1 for invalid
+ * input or a failed cell (k_max reached in section 3, or T(e) lost); unlike chem_advance, a failed
+ * cell keeps the state it had reached.  chem_status reports nbulk = cells finished in section 2,
+ * nqueued = cells entering section 3, substeps = attempts = explicit substeps.  *launches (may be
+ * NULL) receives the number of section-2 launches.  Synchronizes `stream` after every launch (the
+ * host reads the active count), so it is not graph-capturable.  Allocates 16 * max_cells bytes on
+ * first use.  Dense mechanisms only (CHEM_EUNSUPPORTED for the warp-per-cell path); CHEM_EINVAL
+ * for k_steps < 1 or n_star < 0. */
+int chem_advance_explicit(chem_ctx *ctx, float *T, float *p, float *Y, int64_t ld, const float *rho,
+                          const float *e, int64_t n, double dt, int32_t *substeps, int32_t k_steps,
+                          int64_t n_star, int32_t *launches, void *stream);
+
 /* One box of a block-structured AMR hierarchy (Sec. 2.3): its own SoA arrays (device memory,
  * caller-owned; the same meaning and layout as the arguments of chem_advance) and its chemistry
  * step dt (under temporal subcycling a level-l box advances dt0 / r^l).  level is informational. */

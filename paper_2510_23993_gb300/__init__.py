@@ -102,6 +102,7 @@ def lib():
         L.chem_advance.argtypes = adv
         L.chem_advance_f64.argtypes = adv
         L.chem_advance_host.argtypes = [vp, vp, vp, vp, vp, vp, i64, d, vp, vp]
+        L.chem_advance_explicit.argtypes = [vp, vp, vp, vp, i64, vp, vp, i64, d, vp, i32, i64, _P(i32), vp]
         L.chem_state_from_TpY.argtypes = [vp, vp, vp, vp, i64, i64, vp, vp, vp]
         L.chem_state_from_TpY_f64.argtypes = [vp, vp, vp, vp, i64, i64, vp, vp, vp]
         L.chem_temperature.argtypes = [vp, vp, i64, vp, i64, vp, vp]
@@ -138,7 +139,7 @@ def lib():
         L.chem_strerror.argtypes = [i32]
         L.chem_strerror.restype = ctypes.c_char_p
         for name in ("chem_init", "chem_set_params", "chem_advance", "chem_advance_f64", "chem_advance_host",
-                     "chem_state_from_TpY", "chem_state_from_TpY_f64", "chem_temperature", "chem_rates",
+                     "chem_advance_explicit", "chem_state_from_TpY", "chem_state_from_TpY_f64", "chem_temperature", "chem_rates",
                      "chem_status"):
             getattr(L, name).restype = i32
         _lib = L
@@ -224,6 +225,14 @@ def chem_advance(ctx, T, p, Y, ld, rho, e, n, dt, substeps, stream=None):
 def chem_advance_host(ctx, T, p, Y, rho, e, n, dt, substeps, stream=None):
     return lib().chem_advance_host(ctx, _dp(T), _dp(p), _dp(Y), _dp(rho), _dp(e), int(n), float(dt),
                                    _dp(substeps), _stream(stream))
+
+
+def chem_advance_explicit(ctx, T, p, Y, ld, rho, e, n, dt, substeps, k_steps=5, n_star=10000, stream=None):
+    """The paper's explicit scheme under Algorithm 3's bulk/sparse control; returns (code, launches)."""
+    nl = ctypes.c_int32(0)
+    rc = lib().chem_advance_explicit(ctx, _dp(T), _dp(p), _dp(Y), int(ld), _dp(rho), _dp(e), int(n), float(dt),
+                                     _dp(substeps), int(k_steps), int(n_star), ctypes.byref(nl), _stream(stream))
+    return rc, nl.value
 
 
 def chem_advance_noalloc(mech, params, T, p, Y, ld, rho, e, n, dt, substeps, stats=None, stream=None):
@@ -370,6 +379,16 @@ class Context:
     def advance(self, T, p, Y, rho, e, dt, substeps, stream=None):
         n = self._check_state(T, Y, p, rho, e, substeps)
         _check(chem_advance(self.handle, T, p, Y, Y.stride(0), rho, e, n, dt, substeps, stream), "chem_advance")
+
+    def advance_explicit(self, T, p, Y, rho, e, dt, substeps, k_steps=5, n_star=10000, stream=None):
+        """Explicit first-order scheme of Sec. 2.1 under Algorithm 3 (bulk launches of k_steps
+        substeps while more than n_star cells are active, then one sparse launch); returns the
+        number of bulk launches.  Synchronizes the stream."""
+        n = self._check_state(T, Y, p, rho, e, substeps)
+        rc, nl = chem_advance_explicit(self.handle, T, p, Y, Y.stride(0), rho, e, n, dt, substeps, k_steps, n_star,
+                                       stream)
+        _check(rc, "chem_advance_explicit")
+        return nl
 
     def advance_host(self, T, p, Y, rho, e, dt, substeps, stream=None):
         _check(chem_advance_host(self.handle, T, p, Y, rho, e, T.shape[0], dt, substeps, stream),

@@ -56,6 +56,8 @@ struct chem_ctx {
   unsigned char* cont_key = nullptr;
   int* cont_sorted = nullptr;
   long long cont_cap = 0;
+  // chem_advance_explicit: time and FP64 temperature of each cell (allocated on first use)
+  double* tcell = nullptr;
 };
 
 namespace {
@@ -70,7 +72,6 @@ unsigned align16(unsigned x) { return (x + 15u) & ~15u; }
 
 bool compiled_ns(int ns) { return ns == 9; }
 
-// Host-side packing of the mechanism into the device blob layout of chem_device.cuh.
 // Host-side packing of the mechanism into the device blob layout of chem_device.cuh.  The dense
 // layout (ns <= 15) holds full stoichiometric rows and FP64 copies of the rate tables; the large
 // layout (large.cu) holds packed sparse stoichiometry and a species -> reaction index instead, and
@@ -575,12 +576,92 @@ void chem_destroy(chem_ctx* ctx) {
   cudaFree(ctx->cont_list);
   cudaFree(ctx->cont_key);
   cudaFree(ctx->cont_sorted);
+  cudaFree(ctx->tcell);
   delete ctx;
 }
 
 int chem_advance(chem_ctx* ctx, float* T, float* p, float* Y, int64_t ld, const float* rho, const float* e,
                  int64_t n, double dt, int32_t* substeps, void* stream) {
   return advance_impl<float>(ctx, T, p, Y, ld, rho, e, n, dt, substeps, static_cast<cudaStream_t>(stream));
+}
+
+int chem_advance_explicit(chem_ctx* ctx, float* T, float* p, float* Y, int64_t ld, const float* rho, const float* e,
+                          int64_t n, double dt, int32_t* substeps, int32_t k_steps, int64_t n_star,
+                          int32_t* launches, void* stream) {
+  if (launches) *launches = 0;
+  if (!ctx || n < 0 || !(dt > 0) || !std::isfinite(dt) || k_steps < 1 || n_star < 0) return CHEM_EINVAL;
+  if (ctx->large) return CHEM_EUNSUPPORTED;
+  if (n > ctx->max_cells) return CHEM_ENOMEM;
+  if (n > 0 && (!T || !Y || !rho || !e || !substeps || ld < n)) return CHEM_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int rc = cuda_fail(cudaSetDevice(ctx->dev), "cudaSetDevice");
+  if (rc) return rc;
+  if (!ctx->tcell && ctx->max_cells > 0) {
+    rc = cuda_fail(cudaMalloc(&ctx->tcell, 2 * sizeof(double) * ctx->max_cells), "cudaMalloc(tcell)");
+    if (rc) return rc;
+  }
+  rc = cuda_fail(cudaMemsetAsync(ctx->ws, 0, sizeof(Workspace), st), "cudaMemsetAsync");
+  if (rc) return rc;
+  ctx->last_n = n;
+  ctx->timed = false;
+  if (n > 0) {
+    AdvanceArgs<float> a{};
+    a.blob = ctx->blob;
+    a.blob_bytes = ctx->blob_bytes;
+    a.prm = kparams(ctx->prm);
+    a.T = T;
+    a.p = p;
+    a.Y = Y;
+    a.ld = ld;
+    a.rho = rho;
+    a.e = e;
+    a.n = n;
+    a.dt = dt;
+    a.substeps = substeps;
+    a.ws = ctx->ws;
+    a.queue = ctx->queue;
+    const long long want = (n + kBulkBlock - 1) / kBulkBlock;
+    const int grid = static_cast<int>(want < ctx->bulk_grid ? want : ctx->bulk_grid);
+    // the active count after a launch, copied to the host (Algorithm 3, copy_device2host)
+    auto active = [&](long long* out) {
+      int r = cuda_fail(cudaMemcpyAsync(&ctx->ws_host->qcount, &ctx->ws->qcount, sizeof(int), cudaMemcpyDeviceToHost, st),
+                        "cudaMemcpyAsync(count)");
+      if (!r) r = cuda_fail(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+      *out = ctx->ws_host->qcount;
+      return r;
+    };
+    // section 1: times, activity test, first active list
+    int r = launch_explicit(ctx->ns, a, ctx->tcell, kExInit, 0, grid, st);
+    if (r == -1) return CHEM_EUNSUPPORTED;
+    if (r) return cuda_fail(static_cast<cudaError_t>(r), "kernel launch");
+    long long n_active = 0;
+    rc = active(&n_active);
+    if (rc) return rc;
+    // section 2: bulk launches of at most k_steps substeps per cell while N_active > N*; the
+    // launches are capped so that no cell takes more than k_max substeps in this phase
+    const long long cap = (static_cast<long long>(ctx->prm.k_max) + k_steps - 1) / k_steps;
+    long long nl = 0;
+    while (n_active > n_star && nl < cap) {
+      rc = cuda_fail(cudaMemsetAsync(&ctx->ws->qcount, 0, sizeof(int), st), "cudaMemsetAsync");
+      if (rc) return rc;
+      r = launch_explicit(ctx->ns, a, ctx->tcell, kExBulk, k_steps, grid, st);
+      if (r) return cuda_fail(static_cast<cudaError_t>(r), "kernel launch");
+      ++nl;
+      rc = active(&n_active);
+      if (rc) return rc;
+    }
+    if (launches) *launches = static_cast<int32_t>(nl);
+    // section 3: the listed active cells, at most k_max substeps each
+    if (n_active > 0) {
+      const long long sg = (n_active + kBulkBlock - 1) / kBulkBlock;
+      r = launch_explicit(ctx->ns, a, ctx->tcell, kExSparse, ctx->prm.k_max, static_cast<int>(sg), st);
+      if (r) return cuda_fail(static_cast<cudaError_t>(r), "kernel launch");
+    }
+  }
+  rc = cuda_fail(cudaMemcpyAsync(ctx->ws_host, ctx->ws, sizeof(Workspace), cudaMemcpyDeviceToHost, st),
+                 "cudaMemcpyAsync(stats)");
+  if (rc) return rc;
+  return cuda_fail(cudaStreamSynchronize(st), "cudaStreamSynchronize");
 }
 
 int chem_advance_f64(chem_ctx* ctx, double* T, double* p, double* Y, int64_t ld, const double* rho,

@@ -150,6 +150,11 @@ size_t bulk_smem_bytes(unsigned blob_bytes, int nbox);
 int stiff_occupancy(int ns, unsigned blob_bytes, int* blocks_per_sm);
 int bulk_occupancy(int ns, bool f64, unsigned blob_bytes, int* blocks_per_sm);
 
+// the paper's explicit integration loop (explicit.cu)
+constexpr int kExInit = 0, kExBulk = 1, kExSparse = 2;
+int launch_explicit(int ns, const AdvanceArgs<float>& a, double* tcell, int mode, int max_sub, int grid,
+                    cudaStream_t s);
+
 // large mechanisms (large.cu): one warp per cell, sparse stoichiometry
 bool compiled_large(int ns);
 int launch_bulk_lg(int ns, int nr, int ntb, const AdvanceArgs<float>& a, int grid, cudaStream_t s);
