@@ -172,8 +172,9 @@ int chem_advance_host(chem_ctx *ctx, float *T, float *p, float *Y, const float *
  * cell keeps the state it had reached.  chem_status reports nbulk = cells finished in section 2,
  * nqueued = cells entering section 3, substeps = attempts = explicit substeps.  *launches (may be
  * NULL) receives the number of section-2 launches.  Synchronizes `stream` after every launch (the
- * host reads the active count), so it is not graph-capturable.  Allocates 16 * max_cells bytes on
- * first use.  Dense mechanisms only (CHEM_EUNSUPPORTED for the warp-per-cell path); CHEM_EINVAL
+ * host reads the active count), so it is not graph-capturable.  Allocates 8 * (ns + 2) * max_cells
+ * bytes on first use (each cell's time, temperature and Y in FP64 between launches).  FP64 state
+ * arithmetic; rates in FP32, or FP64 with CHEM_FLAG_FP64_RATES.  Dense mechanisms only (CHEM_EUNSUPPORTED for the warp-per-cell path); CHEM_EINVAL
  * for k_steps < 1 or n_star < 0. */
 int chem_advance_explicit(chem_ctx *ctx, float *T, float *p, float *Y, int64_t ld, const float *rho,
                           const float *e, int64_t n, double dt, int32_t *substeps, int32_t k_steps,

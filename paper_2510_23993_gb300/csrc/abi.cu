@@ -56,8 +56,8 @@ struct chem_ctx {
   unsigned char* cont_key = nullptr;
   int* cont_sorted = nullptr;
   long long cont_cap = 0;
-  // chem_advance_explicit: time and FP64 temperature of each cell (allocated on first use)
-  double* tcell = nullptr;
+  // chem_advance_explicit: FP64 time, temperature and mass fractions of each cell (first use)
+  double* xcell = nullptr;
 };
 
 namespace {
@@ -576,7 +576,7 @@ void chem_destroy(chem_ctx* ctx) {
   cudaFree(ctx->cont_list);
   cudaFree(ctx->cont_key);
   cudaFree(ctx->cont_sorted);
-  cudaFree(ctx->tcell);
+  cudaFree(ctx->xcell);
   delete ctx;
 }
 
@@ -596,8 +596,8 @@ int chem_advance_explicit(chem_ctx* ctx, float* T, float* p, float* Y, int64_t l
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   int rc = cuda_fail(cudaSetDevice(ctx->dev), "cudaSetDevice");
   if (rc) return rc;
-  if (!ctx->tcell && ctx->max_cells > 0) {
-    rc = cuda_fail(cudaMalloc(&ctx->tcell, 2 * sizeof(double) * ctx->max_cells), "cudaMalloc(tcell)");
+  if (!ctx->xcell && ctx->max_cells > 0) {
+    rc = cuda_fail(cudaMalloc(&ctx->xcell, sizeof(double) * (ctx->ns + 2) * ctx->max_cells), "cudaMalloc(xcell)");
     if (rc) return rc;
   }
   rc = cuda_fail(cudaMemsetAsync(ctx->ws, 0, sizeof(Workspace), st), "cudaMemsetAsync");
@@ -631,7 +631,7 @@ int chem_advance_explicit(chem_ctx* ctx, float* T, float* p, float* Y, int64_t l
       return r;
     };
     // section 1: times, activity test, first active list
-    int r = launch_explicit(ctx->ns, a, ctx->tcell, kExInit, 0, grid, st);
+    int r = launch_explicit(ctx->ns, a, ctx->xcell, kExInit, 0, grid, st);
     if (r == -1) return CHEM_EUNSUPPORTED;
     if (r) return cuda_fail(static_cast<cudaError_t>(r), "kernel launch");
     long long n_active = 0;
@@ -644,7 +644,7 @@ int chem_advance_explicit(chem_ctx* ctx, float* T, float* p, float* Y, int64_t l
     while (n_active > n_star && nl < cap) {
       rc = cuda_fail(cudaMemsetAsync(&ctx->ws->qcount, 0, sizeof(int), st), "cudaMemsetAsync");
       if (rc) return rc;
-      r = launch_explicit(ctx->ns, a, ctx->tcell, kExBulk, k_steps, grid, st);
+      r = launch_explicit(ctx->ns, a, ctx->xcell, kExBulk, k_steps, grid, st);
       if (r) return cuda_fail(static_cast<cudaError_t>(r), "kernel launch");
       ++nl;
       rc = active(&n_active);
@@ -654,7 +654,7 @@ int chem_advance_explicit(chem_ctx* ctx, float* T, float* p, float* Y, int64_t l
     // section 3: the listed active cells, at most k_max substeps each
     if (n_active > 0) {
       const long long sg = (n_active + kBulkBlock - 1) / kBulkBlock;
-      r = launch_explicit(ctx->ns, a, ctx->tcell, kExSparse, ctx->prm.k_max, static_cast<int>(sg), st);
+      r = launch_explicit(ctx->ns, a, ctx->xcell, kExSparse, ctx->prm.k_max, static_cast<int>(sg), st);
       if (r) return cuda_fail(static_cast<cudaError_t>(r), "kernel launch");
     }
   }

@@ -4,28 +4,31 @@
 // y_floor, and never past the end of the step) driven by Algorithm 3: a counting launch over all
 // cells (section 1), bulk launches over all cells of at most K substeps per cell while the active
 // count read back on the host exceeds N* (section 2), then one launch over the compacted active
-// cells with at most k_max substeps each (section 3).  One thread per cell; FP32 state and rates,
-// FP64 time and the FP64 temperature inversion after every substep.
+// cells with at most k_max substeps each (section 3).  One thread per cell; FP64 state, time and
+// temperature inversion after every substep; rates in FP32 (FP64 with CHEM_FLAG_FP64_RATES).
 #include "chem_device.cuh"
 #include "internal.h"
 
 namespace chem {
 
-// mode kExInit: section 1 (time 0 or dt, count and list the active cells);
+// mode kExInit: section 1 (time 0 or dt, T from e, count and list the active cells);
 // mode kExBulk: every cell still short of dt takes up to max_sub substeps, survivors are listed;
 // mode kExSparse: the listed cells take up to max_sub substeps, survivors fail.
-// tcell[2n] holds each cell's time within the step and its FP64 temperature, so that a cell's
-// sequence of substeps does not depend on how the launches split it; the active list is
-// a.queue / a.ws->qcount.
+// x[(ns + 2) n] carries each active cell's time, temperature and mass fractions in FP64 between
+// launches (SoA: t, T, Y_0 .. Y_{ns-1}), so that a cell's sequence of substeps does not depend on
+// how the launches split it; the FP32 arrays receive the state when a cell finishes or fails.
+// The active list is a.queue / a.ws->qcount.
 template <int NS>
-__global__ void __launch_bounds__(kBulkBlock) explicit_kernel(const AdvanceArgs<float> a, double* tcell, int mode,
+__global__ void __launch_bounds__(kBulkBlock) explicit_kernel(const AdvanceArgs<float> a, double* x, int mode,
                                                                int max_sub) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ uint64_t bar;
   if (!stage_to_smem(smem, a.blob, a.blob_bytes, &bar, &a.ws->status)) return;
   const MechView m = make_view(smem);
   const long long cnt = mode == kExSparse ? static_cast<long long>(a.ws->qcount) : a.n;
+  const long long n = a.n;
   const double dt = a.dt;
+  const bool fp64 = (a.prm.flags & 1) != 0;   // CHEM_FLAG_FP64_RATES
   unsigned long long c_sub = 0, c_skip = 0, c_inv = 0, c_fail = 0, c_done = 0;
   int flags = 0;
   const int lane = threadIdx.x & 31;
@@ -39,10 +42,12 @@ __global__ void __launch_bounds__(kBulkBlock) explicit_kernel(const AdvanceArgs<
       if (mode == kExInit) {
         const float rho = a.rho[i], e = a.e[i], T = a.T[i];
         bool valid = isfinite(rho) && rho > 0.0f && isfinite(e) && isfinite(T) && T > 0.0f;
+        double y[NS];
 #pragma unroll
         for (int k = 0; k < NS; ++k) {
-          const float y = a.Y[k * a.ld + i];
-          valid = valid && isfinite(y) && y > -1e-6f;
+          const float yk = a.Y[k * a.ld + i];
+          valid = valid && isfinite(yk) && yk > -1e-6f;
+          y[k] = yk;
         }
         if (!valid) {
           a.substeps[i] = -1;
@@ -50,48 +55,54 @@ __global__ void __launch_bounds__(kBulkBlock) explicit_kernel(const AdvanceArgs<
         } else if (T < a.prm.T_min) {
           a.substeps[i] = 0;
           ++c_skip;
-        } else {   // the cell's temperature from e, carried in FP64 by the later launches
-          float y[NS];
-#pragma unroll
-          for (int k = 0; k < NS; ++k) y[k] = a.Y[k * a.ld + i];
+        } else {
           bool ok;
-          tcell[a.n + i] = temperature_from_energy<NS>(m, y, static_cast<double>(e), static_cast<double>(T), &ok);
+          const double T0 = temperature_from_energy<NS>(m, y, static_cast<double>(e), static_cast<double>(T), &ok);
           a.substeps[i] = ok ? 0 : -1;
           active = ok;
-          if (!ok) {
+          if (ok) {
+            x[n + i] = T0;
+#pragma unroll
+            for (int k = 0; k < NS; ++k) x[(2 + k) * n + i] = y[k];
+          } else {
             ++c_fail;
             flags |= kFlagTemp;
           }
         }
-        tcell[i] = active ? 0.0 : dt;
-      } else if (tcell[i] < dt) {
-        double t = tcell[i];
+        x[i] = active ? 0.0 : dt;
+      } else if (x[i] < dt) {
+        double t = x[i], T = x[n + i];
         const float rho = a.rho[i];
         const double e = a.e[i];
-        float y[NS];
+        double y[NS];
 #pragma unroll
-        for (int k = 0; k < NS; ++k) y[k] = a.Y[k * a.ld + i];
+        for (int k = 0; k < NS; ++k) y[k] = x[(2 + k) * n + i];
         bool ok = true;
-        double T = tcell[a.n + i];
         int s = 0;
 #pragma unroll 1
         for (; s < max_sub && ok && t < dt; ++s) {
-          float f[NS], y1[NS];
-          ok = rates<NS, float>(m, rho, static_cast<float>(T), y, f);
+          double f[NS], y1[NS];
+          if (fp64) {
+            rates<NS, double>(m, static_cast<double>(rho), T, y, f);
+          } else {   // FP32 rates (FP64 where the FP32 log-rates overflow)
+            float ff[NS];
+            rates_safe<NS>(m, rho, T, y, ff);
+#pragma unroll
+            for (int k = 0; k < NS; ++k) f[k] = ff[k];
+          }
           // the longest substep that changes no Y_k by more than bulk_frac of max(|Y_k|, y_floor)
           const double rem = dt - t;
           double h = rem;
 #pragma unroll
           for (int k = 0; k < NS; ++k) {
-            const float af = fabsf(f[k]);
-            if (af > 0.0f) h = fmin(h, static_cast<double>(a.prm.bulk_frac * fmaxf(fabsf(y[k]), a.prm.y_floor) / af));
+            const double af = fabs(f[k]);
+            if (af > 0.0) h = fmin(h, static_cast<double>(a.prm.bulk_frac) * fmax(fabs(y[k]), static_cast<double>(a.prm.y_floor)) / af);
           }
-          const float hf = static_cast<float>(h);
 #pragma unroll
-          for (int k = 0; k < NS; ++k) y1[k] = fmaf(hf, f[k], y[k]);
+          for (int k = 0; k < NS; ++k) y1[k] = fma(h, f[k], y[k]);
           bool okT;
           const double T1 = temperature_from_energy<NS>(m, y1, e, T, &okT);
-          ok = ok && okT;
+          ok = okT;
           if (ok) {
 #pragma unroll
             for (int k = 0; k < NS; ++k) y[k] = y1[k];
@@ -100,16 +111,9 @@ __global__ void __launch_bounds__(kBulkBlock) explicit_kernel(const AdvanceArgs<
           }
         }
         c_sub += s;
-        double sw = 0.0;
-#pragma unroll
-        for (int k = 0; k < NS; ++k) {
-          a.Y[k * a.ld + i] = y[k];
-          sw = fma(static_cast<double>(y[k]), static_cast<double>(m.invW[k]), sw);
-        }
-        a.T[i] = static_cast<float>(T);
-        if (a.p) a.p[i] = static_cast<float>(static_cast<double>(rho) * kR * T * sw);
         active = ok && t < dt;
-        if (!ok || (active && mode == kExSparse)) {   // temperature lost, or k_max reached
+        const bool fail = !ok || (active && mode == kExSparse);   // T(e) lost, or k_max reached
+        if (fail) {
           flags |= ok ? kFlagMaxSteps : kFlagTemp;
           a.substeps[i] = -1;
           t = dt;
@@ -119,8 +123,21 @@ __global__ void __launch_bounds__(kBulkBlock) explicit_kernel(const AdvanceArgs<
           a.substeps[i] += s;
           if (!active && mode == kExBulk) ++c_done;
         }
-        tcell[i] = t;
-        tcell[a.n + i] = T;
+        x[i] = t;
+        if (active) {
+          x[n + i] = T;
+#pragma unroll
+          for (int k = 0; k < NS; ++k) x[(2 + k) * n + i] = y[k];
+        } else {   // finished or failed: the state reached goes to the FP32 arrays
+          double sw = 0.0;
+#pragma unroll
+          for (int k = 0; k < NS; ++k) {
+            a.Y[k * a.ld + i] = static_cast<float>(y[k]);
+            sw = fma(y[k], static_cast<double>(m.invW[k]), sw);
+          }
+          a.T[i] = static_cast<float>(T);
+          if (a.p) a.p[i] = static_cast<float>(static_cast<double>(rho) * kR * T * sw);
+        }
       }
     }
     // compaction of the cells still active, one atomic per warp (section 3's index list)
@@ -160,14 +177,14 @@ __global__ void __launch_bounds__(kBulkBlock) explicit_kernel(const AdvanceArgs<
   }
 }
 
-int launch_explicit(int ns, const AdvanceArgs<float>& a, double* tcell, int mode, int max_sub, int grid,
+int launch_explicit(int ns, const AdvanceArgs<float>& a, double* x, int mode, int max_sub, int grid,
                     cudaStream_t s) {
   if (ns != 9) return -1;
   const size_t smem = (a.blob_bytes + 127u) & ~127u;
   cudaError_t e = cudaFuncSetAttribute(explicit_kernel<9>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(smem));
   if (e != cudaSuccess) return static_cast<int>(e);
-  explicit_kernel<9><<<grid, kBulkBlock, smem, s>>>(a, tcell, mode, max_sub);
+  explicit_kernel<9><<<grid, kBulkBlock, smem, s>>>(a, x, mode, max_sub);
   return static_cast<int>(cudaGetLastError());
 }
 
