@@ -441,6 +441,117 @@ def run_reference(args, world):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def _time_ms(fn, reps, torch):
+    """Median CUDA-event time of fn() over reps calls (after one warm-up call)."""
+    fn()
+    out = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        out.append(a.elapsed_time(b))
+    return float(np.median(out))
+
+
+def run_study(args):
+    """Comparisons with the paper's baseline strategies (one JSON line per measurement):
+      rates:  the multi-kernel cuBLAS rate evaluation (chem_mk_rates) against the fused kernel
+              (chem_rates), one grid of n cells (App. C) and 1M cells split into G grids, one
+              launch sequence per grid (Sec. 3.2.1, App. E), for the 9- and 53-species mechanisms;
+      fusion: one chemistry step of 1M cells split into G boxes, advanced box by box
+              (chem_advance per box) against one fused launch over the box table (graph replay)."""
+    import torch
+    import paper_2510_23993_gb300 as chem
+    chem.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+    if args.study == "rates":
+        for name, mech in (("9 species / 21 reactions", synth.h2_air_mechanism(0)),
+                           ("53 species / 325 reactions", synth.hydrocarbon_mechanism(0))):
+            N = 1 << 20
+            rng = np.random.default_rng(0)
+            T = rng.uniform(800, 3000, N).astype(np.float32)
+            p = (rng.uniform(1, 20, N) * synth.P_ATM).astype(np.float32)
+            Y = np.ascontiguousarray(rng.dirichlet(np.full(mech["ns"], 0.3), size=N).T, dtype=np.float32)
+            ctx = chem.Context(mech, max_cells=N)
+            mk = chem.MultiKernelRates(mech, max_cells=N)
+            tT, tp, tY = (torch.from_numpy(a).to(dev) for a in (T, p, Y))
+            rho, e = torch.empty_like(tT), torch.empty_like(tT)
+            ctx.state_from_TpY(tT, tp, tY, rho, e)
+            f = torch.empty_like(tY)
+            for n in (1000, 10000, 100000, N):
+                Ys = tY[:, :n].contiguous()
+                fs = f[:, :n].contiguous()
+                t_f = _time_ms(lambda: ctx.rates(rho[:n], tT[:n], Ys, fs), args.steps, torch)
+                t_m = _time_ms(lambda: mk.rates(rho[:n], tT[:n], Ys, fs), args.steps, torch)
+                print(json.dumps({"study": "rates_one_grid", "mechanism": name, "cells": n, "fused_ms": t_f,
+                                  "multikernel_ms": t_m, "multikernel_over_fused": t_m / t_f}), flush=True)
+            for G in (1, 15, 150, 1000):
+                off = np.linspace(0, N, G + 1).astype(np.int64)
+
+                def per_grid():
+                    for g in range(G):
+                        a, b = int(off[g]), int(off[g + 1])
+                        mk.rates(rho[a:], tT[a:], tY[:, a:], f[:, a:], n=b - a)
+
+                t_m = _time_ms(per_grid, args.steps, torch)
+                t_f = _time_ms(lambda: chem.chem_rates(ctx.handle, rho, tT, tY, N, N, f), args.steps, torch)
+                print(json.dumps({"study": "rates_grids", "mechanism": name, "cells": N, "grids": G,
+                                  "fused_one_launch_ms": t_f, "multikernel_per_grid_ms": t_m,
+                                  "launches_multikernel": G * (5 if mech["third_body"].any() else 4),
+                                  "multikernel_over_fused": t_m / t_f}), flush=True)
+            mk.close()
+            ctx.close()
+    else:   # fusion of the whole chemistry step across boxes
+        mech = synth.h2_air_mechanism(0)
+        T, p, Y, hot = synth.sheet_field(mech, n=100, seed=0)
+        T, p, Y = T.astype(np.float32), p.astype(np.float32), np.ascontiguousarray(Y, dtype=np.float32)
+        N = T.size
+        ctx = chem.Context(mech, max_cells=N)
+        tT, tp, tY = (torch.from_numpy(a).to(dev) for a in (T, p, Y))
+        rho, e = torch.empty_like(tT), torch.empty_like(tT)
+        ctx.state_from_TpY(tT, tp, tY, rho, e)
+        T0, Y0 = tT.clone(), tY.clone()
+        sub = torch.zeros(N, dtype=torch.int32, device=dev)
+        stream = torch.cuda.Stream()
+        for G in (1, 15, 150, 1000):
+            off = np.linspace(0, N, G + 1).astype(np.int64)
+            boxes = [dict(T=tT[a:b], p=tp[a:b], Y=tY[:, a:b], rho=rho[a:b], e=e[a:b], substeps=sub[a:b], dt=DT,
+                          level=0) for a, b in zip(off[:-1], off[1:])]
+
+            def per_box():
+                tT.copy_(T0)
+                tY.copy_(Y0)
+                for bx in boxes:
+                    n = bx["T"].shape[0]
+                    chem._check(chem.chem_advance(ctx.handle, bx["T"], bx["p"], bx["Y"], N, bx["rho"], bx["e"], n, DT,
+                                                  bx["substeps"]), "chem_advance")
+
+            t_b = _time_ms(per_box, max(2, args.steps // 2), torch)
+            ctx.set_boxes(boxes)
+            with torch.cuda.stream(stream):
+                tT.copy_(T0)
+                tY.copy_(Y0)
+                ctx.capture_boxes(stream)
+            torch.cuda.synchronize()
+
+            def fused():
+                with torch.cuda.stream(stream):
+                    tT.copy_(T0)
+                    tY.copy_(Y0)
+                    ctx.launch_boxes(stream)
+                stream.synchronize()
+
+            t_f = _time_ms(fused, max(2, args.steps // 2), torch)
+            print(json.dumps({"study": "step_boxes", "cells": N, "boxes": G, "per_box_calls_ms": t_b,
+                              "fused_graph_ms": t_f, "per_box_over_fused": t_b / t_f,
+                              "field": "reacting sheet 100^3, 5% reacting, dt 1e-8 s, boxes = equal slabs"}),
+                  flush=True)
+        ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -470,7 +581,12 @@ def main():
     ap.add_argument("--paper-frac", type=float, default=0.05, help="relative change limit of the explicit scheme")
     ap.add_argument("--train-pairs", type=int, default=262144)
     ap.add_argument("--train-epochs", type=int, default=40)
+    ap.add_argument("--study", default=None, choices=["rates", "fusion"],
+                    help="instead of the benchmark line: the comparisons with the paper's baseline strategies")
     args = ap.parse_args()
+    if args.study:
+        run_study(args)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

@@ -180,6 +180,22 @@ int chem_advance_explicit(chem_ctx *ctx, float *T, float *p, float *Y, int64_t l
                           const float *e, int64_t n, double dt, int32_t *substeps, int32_t k_steps,
                           int64_t n_star, int32_t *launches, void *stream);
 
+/* The multi-kernel, library-GEMM rate evaluation that the paper's fused kernel replaces (Sec.
+ * 3.2.1 and its Fig. 2A baseline; App. C): per call, a cell-parallel preparation kernel, cuBLAS
+ * SGEMMs for the stoichiometric products (ln C . nu_f^T, ln C . nu_r^T, C . eff^T for the
+ * third-body rows), a cells x reactions kernel for the rates of progress, and a final SGEMM
+ * q . (dnu W) that writes dY/dt.  Same inputs, output and precision (FP32) as chem_rates; kept
+ * as the comparison point of the single-kernel strategy, per grid.  chem_mk_create copies the
+ * mechanism, opens cuBLAS at run time (CHEM_EUNSUPPORTED if libcublas cannot be loaded) and
+ * allocates 4 * (2 ns + 2 nr + ntb + 5) bytes per cell of max_cells (ntb: third-body reactions).
+ * chem_mk_rates: device pointers, asynchronous on `stream`, CHEM_ENOMEM if n > max_cells; not
+ * thread-safe (one scratch per object).  chem_mk_destroy synchronizes the device. */
+typedef struct chem_mk chem_mk;
+int chem_mk_create(const chem_mechanism *mech, int64_t max_cells, chem_mk **out);
+int chem_mk_rates(chem_mk *mk, const float *rho, const float *T, const float *Y, int64_t ld, int64_t n,
+                  float *dYdt, void *stream);
+void chem_mk_destroy(chem_mk *mk);
+
 /* One box of a block-structured AMR hierarchy (Sec. 2.3): its own SoA arrays (device memory,
  * caller-owned; the same meaning and layout as the arguments of chem_advance) and its chemistry
  * step dt (under temporal subcycling a level-l box advances dt0 / r^l).  level is informational. */

@@ -103,6 +103,12 @@ def lib():
         L.chem_advance_f64.argtypes = adv
         L.chem_advance_host.argtypes = [vp, vp, vp, vp, vp, vp, i64, d, vp, vp]
         L.chem_advance_explicit.argtypes = [vp, vp, vp, vp, i64, vp, vp, i64, d, vp, i32, i64, _P(i32), vp]
+        L.chem_mk_create.argtypes = [_P(chem_mechanism), i64, _P(vp)]
+        L.chem_mk_create.restype = i32
+        L.chem_mk_rates.argtypes = [vp, vp, vp, vp, i64, i64, vp, vp]
+        L.chem_mk_rates.restype = i32
+        L.chem_mk_destroy.argtypes = [vp]
+        L.chem_mk_destroy.restype = None
         L.chem_state_from_TpY.argtypes = [vp, vp, vp, vp, i64, i64, vp, vp, vp]
         L.chem_state_from_TpY_f64.argtypes = [vp, vp, vp, vp, i64, i64, vp, vp, vp]
         L.chem_temperature.argtypes = [vp, vp, i64, vp, i64, vp, vp]
@@ -341,6 +347,36 @@ def chem_status(ctx, stream=None):
 
 def chem_strerror(code):
     return lib().chem_strerror(int(code)).decode()
+
+
+class MultiKernelRates:
+    """The multi-kernel, cuBLAS-GEMM rate evaluation (chem_mk_*): the per-grid baseline strategy
+    that the fused single-kernel chem_rates replaces (Sec. 3.2.1, App. C)."""
+
+    def __init__(self, mech, max_cells):
+        self.mech = mech if isinstance(mech, Mechanism) else Mechanism(mech)
+        h = ctypes.c_void_p()
+        _check(lib().chem_mk_create(ctypes.byref(self.mech.c), int(max_cells), ctypes.byref(h)), "chem_mk_create")
+        self.handle = h
+
+    def close(self):
+        if self.handle:
+            lib().chem_mk_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def rates(self, rho, T, Y, dYdt, n=None, stream=None):
+        n = T.shape[0] if n is None else n
+        for t in (rho, T, Y, dYdt):
+            if not t.is_cuda:
+                raise ValueError("tensors must be CUDA tensors")
+        _check(lib().chem_mk_rates(self.handle, _dp(rho), _dp(T), _dp(Y), Y.stride(0), int(n), _dp(dYdt),
+                                   _stream(stream)), "chem_mk_rates")
 
 
 class Context:

@@ -12,7 +12,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libchem.so")
-SOURCES = ["abi.cu", "bulk.cu", "stiff.cu", "noalloc.cu", "tune.cu", "mlp.cu", "surrogate.cu", "large.cu", "explicit.cu"]
+SOURCES = ["abi.cu", "bulk.cu", "stiff.cu", "noalloc.cu", "tune.cu", "mlp.cu", "surrogate.cu", "large.cu", "explicit.cu", "multikernel.cu"]
 HEADERS = ["chem_device.cuh", "internal.h", "tc.cuh"]
 NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -53,7 +53,7 @@ def build(force=False, verbose=False, extra_flags=()):
         list(ex.map(run, jobs))
     if force or jobs or _stale(LIB, objs):
         tmp = LIB + f".tmp{os.getpid()}"
-        run([NVCC] + ARCH + ["-shared", "-cudart", "static", "-o", tmp] + objs)
+        run([NVCC] + ARCH + ["-shared", "-cudart", "static", "-o", tmp] + objs + ["-ldl"])
         os.replace(tmp, LIB)
     return LIB
 
