@@ -461,12 +461,33 @@ def run_study(args):
               (chem_rates), one grid of n cells (App. C) and 1M cells split into G grids, one
               launch sequence per grid (Sec. 3.2.1, App. E), for the 9- and 53-species mechanisms;
       fusion: one chemistry step of 1M cells split into G boxes, advanced box by box
-              (chem_advance per box) against one fused launch over the box table (graph replay)."""
+              (chem_advance per box) against one fused launch over the box table (graph replay);
+      layout: the state load (chem_pressure_layout) from ~1.5 GiB of records in each storage
+              layout, in HBM GB/s."""
     import torch
     import paper_2510_23993_gb300 as chem
     chem.build()
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(0)
+    if args.study == "layout":
+        peaks = os.path.join(ROOT, "MEASURED_PEAKS.json")
+        hbm = json.load(open(peaks)).get("hbm_gbs") if os.path.exists(peaks) else None
+        names = {chem.CHEM_LAYOUT_SOA: "SoA (component-major)", chem.CHEM_LAYOUT_AOS: "AoS (cell-major)",
+                 chem.CHEM_LAYOUT_AOSOA: "AoSoA (32-cell tiles)", chem.CHEM_LAYOUT_AOS_STAGED: "AoS staged in shared memory"}
+        for label, mech in (("9 species", synth.h2_air_mechanism(0)), ("53 species", synth.hydrocarbon_mechanism(0))):
+            ns = mech["ns"]
+            nv = ns + 2
+            n = (1536 << 20) // (4 * nv) // 128 * 128      # ~1.5 GiB of records, far above L2
+            X = torch.rand(n * nv, dtype=torch.float32, device=dev) + 0.5
+            p = torch.empty(n, dtype=torch.float32, device=dev)
+            for layout, nm in names.items():
+                ms = _time_ms(lambda: chem.pressure_layout(mech["W"], layout, X, n, p, ld=n), args.steps, torch)
+                gbs = n * (nv + 1) * 4 / (ms / 1e3) / 1e9
+                print(json.dumps({"study": "layout", "mechanism": label, "layout": nm, "cells": n,
+                                  "bytes_per_cell": (nv + 1) * 4, "ms": ms, "GB_s": gbs,
+                                  "frac_of_measured_hbm": gbs / hbm if hbm else None}), flush=True)
+            del X, p
+        return
     if args.study == "rates":
         for name, mech in (("9 species / 21 reactions", synth.h2_air_mechanism(0)),
                            ("53 species / 325 reactions", synth.hydrocarbon_mechanism(0))):
@@ -581,7 +602,7 @@ def main():
     ap.add_argument("--paper-frac", type=float, default=0.05, help="relative change limit of the explicit scheme")
     ap.add_argument("--train-pairs", type=int, default=262144)
     ap.add_argument("--train-epochs", type=int, default=40)
-    ap.add_argument("--study", default=None, choices=["rates", "fusion"],
+    ap.add_argument("--study", default=None, choices=["rates", "fusion", "layout"],
                     help="instead of the benchmark line: the comparisons with the paper's baseline strategies")
     args = ap.parse_args()
     if args.study:

@@ -196,6 +196,27 @@ int chem_mk_rates(chem_mk *mk, const float *rho, const float *T, const float *Y,
                   float *dYdt, void *stream);
 void chem_mk_destroy(chem_mk *mk);
 
+/* Storage layouts of a per-cell state record (rho, T, Y_0 .. Y_{ns-1}), nv = ns + 2 floats, for
+ * chem_pressure_layout (the layout question of Sec. 3.1 / Algorithm 1):
+ *   CHEM_LAYOUT_SOA        X[v * ld + i]  (component-major; ld >= n; the library's own layout)
+ *   CHEM_LAYOUT_AOS        X[i * nv + v]  (cell-major), each thread reads its own record
+ *   CHEM_LAYOUT_AOSOA      X[(i / 32) * 32 * nv + v * 32 + i % 32]  (tiles of 32 cells; the
+ *                          array holds ceil(n / 32) full tiles)
+ *   CHEM_LAYOUT_AOS_STAGED the AoS array, read through shared memory: each CTA copies its 128
+ *                          contiguous records with 16-byte loads (X must be 16-byte aligned) */
+#define CHEM_LAYOUT_SOA 0
+#define CHEM_LAYOUT_AOS 1
+#define CHEM_LAYOUT_AOSOA 2
+#define CHEM_LAYOUT_AOS_STAGED 3
+
+/* p[i] = rho R T sum_k Y_k / W_k from the state records X of n cells in the given layout: the
+ * all-components-of-one-cell load of the integrators, one thread per cell, under each layout
+ * (W: host array of ns molar masses, kg/mol).  Device pointers X, p; asynchronous on `stream`
+ * of the current device.  ns must be 9 or 53 (CHEM_EUNSUPPORTED otherwise); CHEM_EINVAL for an
+ * unknown layout, ld < n (SoA), a misaligned X (staged AoS) or a non-positive W. */
+int chem_pressure_layout(int32_t ns, const double *W, int32_t layout, const float *X, int64_t ld,
+                         int64_t n, float *p, void *stream);
+
 /* One box of a block-structured AMR hierarchy (Sec. 2.3): its own SoA arrays (device memory,
  * caller-owned; the same meaning and layout as the arguments of chem_advance) and its chemistry
  * step dt (under temporal subcycling a level-l box advances dt0 / r^l).  level is informational. */

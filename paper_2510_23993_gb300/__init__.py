@@ -109,6 +109,8 @@ def lib():
         L.chem_mk_rates.restype = i32
         L.chem_mk_destroy.argtypes = [vp]
         L.chem_mk_destroy.restype = None
+        L.chem_pressure_layout.argtypes = [i32, vp, i32, vp, i64, i64, vp, vp]
+        L.chem_pressure_layout.restype = i32
         L.chem_state_from_TpY.argtypes = [vp, vp, vp, vp, i64, i64, vp, vp, vp]
         L.chem_state_from_TpY_f64.argtypes = [vp, vp, vp, vp, i64, i64, vp, vp, vp]
         L.chem_temperature.argtypes = [vp, vp, i64, vp, i64, vp, vp]
@@ -347,6 +349,16 @@ def chem_status(ctx, stream=None):
 
 def chem_strerror(code):
     return lib().chem_strerror(int(code)).decode()
+
+
+CHEM_LAYOUT_SOA, CHEM_LAYOUT_AOS, CHEM_LAYOUT_AOSOA, CHEM_LAYOUT_AOS_STAGED = 0, 1, 2, 3
+
+
+def pressure_layout(W, layout, X, n, p, ld=0, stream=None):
+    """p = rho R T sum_k Y_k / W_k from state records X in one of the CHEM_LAYOUT_* layouts."""
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    _check(lib().chem_pressure_layout(W.size, W.ctypes.data_as(ctypes.c_void_p), int(layout), _dp(X), int(ld), int(n),
+                                      _dp(p), _stream(stream)), "chem_pressure_layout")
 
 
 class MultiKernelRates:
