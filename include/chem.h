@@ -89,11 +89,15 @@ typedef struct {
 #define CHEM_FLAG_ORDER_PREV 8
 /* chem_params.flags: integrate the stiff cells in two passes.  The first pass gives every queued
  * cell up to 32 implicit steps and saves the state of the cells it did not finish; those are
- * then sorted by their estimated remaining steps, (dt - t) / h at the current step size, and the
- * second pass finishes them, longest first.  This starts the expensive cells early, which the
- * tail of the persistent stiff kernel needs when the cost order of ORDER_RATE is inaccurate.
- * Needs 8 * ns + 53 bytes of device memory per cell of max_cells, allocated when the flag is first
- * set (chem_init or chem_set_params); ignored by chem_advance_noalloc. */
+ * sorted by their estimated remaining steps, (dt - t) / h at the current step size.  The second,
+ * cooperative launch takes them longest first from a shared queue; once the queue is empty, each
+ * cell still running is parked after 32 more steps and the parked cells are finished in rounds of
+ * up to 32 steps separated by grid-wide barriers, relisted after each round so that they always
+ * fill whole warps (an FP64 warp instruction costs the same with one active lane as with 32)
+ * spread over all SMs.  Results are bit-identical to the single pass.  Needs 8 * ns + 53 bytes
+ * of device memory per cell of max_cells, allocated when the flag is first set (chem_init or
+ * chem_set_params); ignored by chem_advance_noalloc and by mechanisms of more than 15 species.
+ * A barrier wait longer than 4 s ends the launch and the call reports CHEM_ECUDA. */
 #define CHEM_FLAG_TWO_PASS 16
 
 /* Counters of the last advance call (see chem_status). */

@@ -60,6 +60,10 @@ struct chem_ctx {
   double* xcell = nullptr;
 };
 
+namespace chem {
+int occupancy_stiff(const chem_ctx* c);
+}
+
 namespace {
 
 int cuda_fail(cudaError_t e, const char* what) {
@@ -318,7 +322,9 @@ int ensure_two_pass(chem_ctx* c) {
 }
 
 // The stiff phase: one persistent launch, or (two-pass mode) a probe launch, a counting sort of
-// the unfinished cells by remaining work and a continuation launch.
+// the unfinished cells by remaining work, and a cooperative continuation launch: the sorted cells
+// run to completion from a shared queue until it is empty, then the cells still running are
+// parked and finished in rounds of kRoundAttempts steps, compacted into full warps between rounds.
 template <typename S>
 int launch_stiff_phase(chem_ctx* c, AdvanceArgs<S> b, long long n, cudaStream_t st) {
   auto launch = [&](const AdvanceArgs<S>& x) {
@@ -340,8 +346,12 @@ int launch_stiff_phase(chem_ctx* c, AdvanceArgs<S> b, long long n, cudaStream_t 
   b.pass = 1;
   int r = launch(b);
   if (!r) r = launch_order_queue(c->ws, c->cont_list, c->cont_key, c->cont_sorted, n, st, true);
-  b.pass = 2;
-  if (!r) r = launch(b);
+  b.pass = 2;   // cooperative: every CTA of the grid must be resident at once
+  const int coop = c->sms * occupancy_stiff(c);
+  if (!r) {
+    if constexpr (sizeof(S) == 4) r = launch_stiff_f32(c->ns, b, c->stiff_grid < coop ? c->stiff_grid : coop, st);
+    else r = launch_stiff_f64(c->ns, b, c->stiff_grid < coop ? c->stiff_grid : coop, st);
+  }
   return r;
 }
 

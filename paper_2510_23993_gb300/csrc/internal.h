@@ -10,9 +10,10 @@ struct Workspace {
   int qcount;                    // cells compacted into the stiff queue by the bulk kernel
   int head;                      // next queue slot handed out by the stiff kernel
   int status;                    // OR of kFlag* bits
-  int cont_count;                // two-pass mode: cells the first stiff pass left unfinished
-  int head2;                     // two-pass mode: next continuation handed out by the second pass
-  int pad[3];
+  int cont_count;                // two-pass mode: cells the probe pass left unfinished
+  int head2;                     // two-pass mode: next slot of the sorted continuation list (round 0)
+  int rc[3];                     // two-pass mode: cells left after continuation round r, in rc[r % 3]
+  unsigned bar_count, bar_gen;   // grid barrier of the continuation rounds
   unsigned long long nskipped, nbulk, ninvalid, nfailed, substeps, attempts, newton;
 };
 
@@ -57,14 +58,16 @@ struct AdvanceArgs {
   int nbox;                      // 0: flat arrays T, p, Y, rho, e, substeps of n cells, step dt
   const unsigned char* skip;     // [n] or null: cells with skip[g] != 0 are left untouched (their
                                  //   step was taken elsewhere, e.g. by the surrogate)
-  // two-pass stiff integration (0: single pass; 1: probe pass; 2: continuation pass)
+  // two-pass stiff integration (0: single pass; 1: probe pass; 2: continuation rounds)
   int pass;
   long long cont_cap;            // capacity of the continuation arrays (queue slots)
   double* cont;                  // SoA continuation state by queue slot: y[NS], t, h, T, eta
                                  //   (each [cont_cap] doubles), then float c_v/R, int nst, int natt
-  int* cont_list;                // [cont_cap] queue slots of the unfinished cells (probe pass)
+  int* cont_list;                // [cont_cap] queue slots of the unfinished cells (probe pass),
+                                 //   later the input of odd continuation rounds
   unsigned char* cont_key;       // [cont_cap] their remaining-work bucket
-  int* cont_sorted;              // [cont_cap] the same slots, longest remaining first
+  int* cont_sorted;              // [cont_cap] the same slots, longest remaining first: the input of
+                                 //   round 0, later of even rounds
 };
 
 constexpr int kMaxBoxes = 4096;
@@ -130,6 +133,7 @@ constexpr int kFlagOrderPrev = 8;   // bucket of log2 of the cell's substep coun
 constexpr int kFlagTwoPass = 16;    // two-pass stiff integration
 constexpr int kNumBuckets = 64;
 constexpr int kProbeAttempts = 32;  // implicit steps per cell in the probe pass
+constexpr int kRoundAttempts = 32;  // implicit steps per cell and continuation round
 
 // bytes of continuation state per queue slot
 __host__ __device__ constexpr long long cont_bytes_per_slot(int ns) { return 8LL * (ns + 4) + 12; }

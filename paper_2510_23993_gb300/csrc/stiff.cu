@@ -141,59 +141,97 @@ struct CellCtx {
   bool fp64_rates;
 };
 
-// Solve the stage equation z = yb + hh f(z) by simplified Newton (iteration matrix factored in
-// shared memory) from the initial guess in z.  Tz: temperature guess in, temperature of the
-// last evaluated iterate out.  Convergence is judged on the weighted RMS norm of the update and
-// the contraction rate theta of the iteration: the iterate is accepted when the remaining error
-// predicted from theta, eta * |dz| with eta = theta / (1 - theta), is below kNewtTol.  eta
-// carries over between the stages of a step (first iteration of a stage uses the last value).
+// One simplified-Newton iteration of the stage equation z = yb + hh f(z) (iteration matrix
+// factored in shared memory).  Tz: temperature guess in, temperature of the evaluated iterate
+// out.  Convergence is judged on the weighted RMS norm of the update and the contraction rate
+// theta of the iteration: the iterate is accepted when the remaining error predicted from theta,
+// eta * |dz| with eta = theta / (1 - theta), is below kNewtTol.  eta carries over between the
+// stages of a step (the first iteration of a stage uses the last value).  it and prev hold the
+// stage's iteration count and last norm.  Returns 1 when the stage has converged, 0 to iterate
+// again, -1 on failure (T(e) lost, non-finite or diverging update, kNewtMax iterations).
 template <int NS>
-__device__ __forceinline__ bool stage_newton(const MechView& m, const Smem<NS>& s, uint64_t piv, const CellCtx& c,
-                                             const double (&yb)[NS], double hh, double (&z)[NS], double& Tz,
-                                             double& eta, unsigned long long& n_it) {
-  double prev = 0.0;
-#pragma unroll 1
-  for (int it = 0; it < kNewtMax; ++it) {
-    ++n_it;
-    bool ok;
-    Tz = temperature_from_energy<NS>(m, z, c.e0, Tz, &ok);
-    if (!ok) return false;
-    float F[NS], Zf[NS];
+__device__ __forceinline__ int newton_iteration(const MechView& m, const Smem<NS>& s, uint64_t piv, const CellCtx& c,
+                                                const double (&yb)[NS], double hh, double (&z)[NS], double& Tz,
+                                                float& eta, float& prev, int& it, unsigned long long& n_it) {
+  ++n_it;
+  bool ok;
+  Tz = temperature_from_energy<NS>(m, z, c.e0, Tz, &ok);
+  if (!ok) return -1;
+  float F[NS], Zf[NS];
 #pragma unroll
-    for (int k = 0; k < NS; ++k) Zf[k] = static_cast<float>(z[k]);
-    bool use64 = c.fp64_rates;
-    // FP32 rates; the FP64 instance (one copy in the code) when they overflow
-    if (!use64) use64 = !rates<NS, float>(m, c.rho, static_cast<float>(Tz), Zf, F);
-    if (use64) rates_fp64_fallback<NS>(m, c.rho, Tz, z, F);
-    const float mhh = static_cast<float>(hh);
-    double b[NS];
+  for (int k = 0; k < NS; ++k) Zf[k] = static_cast<float>(z[k]);
+  bool use64 = c.fp64_rates;
+  // FP32 rates; the FP64 instance (one copy in the code) when they overflow
+  if (!use64) use64 = !rates<NS, float>(m, c.rho, static_cast<float>(Tz), Zf, F);
+  if (use64) rates_fp64_fallback<NS>(m, c.rho, Tz, z, F);
+  const float mhh = static_cast<float>(hh);
+  double b[NS];
 #pragma unroll
-    for (int k = 0; k < NS; ++k) b[k] = (yb[k] - z[k]) + static_cast<double>(mhh * F[k]);
-    lu_solve<NS>(s, piv, b);
-    float ss = 0.0f;
+  for (int k = 0; k < NS; ++k) b[k] = (yb[k] - z[k]) + static_cast<double>(mhh * F[k]);
+  lu_solve<NS>(s, piv, b);
+  float ss = 0.0f;
 #pragma unroll
-    for (int k = 0; k < NS; ++k) {
-      z[k] += b[k];
-      const float bf = static_cast<float>(b[k]);
-      const float w = c.atol + c.rtol * fabsf(Zf[k] + bf);
-      const float r = bf / w;
-      ss = fmaf(r, r, ss);
-    }
-    const double nrm = sqrt(static_cast<double>(ss) * (1.0 / NS));
-    if (!(nrm == nrm)) return false;
-    if (it > 0) {
-      const double theta = nrm / prev;
-      if (theta >= 1.0) {
-        // not contracting: accept only at the FP32 noise floor (below half the error weight)
-        if (nrm <= 0.5 && theta < 2.0) return true;
-        return false;
-      }
-      eta = theta / (1.0 - theta);
-    }
-    if (eta * nrm <= kNewtTol || nrm <= 1e-3) return true;
-    prev = nrm;
+  for (int k = 0; k < NS; ++k) {
+    z[k] += b[k];
+    const float bf = static_cast<float>(b[k]);
+    const float w = c.atol + c.rtol * fabsf(Zf[k] + bf);
+    const float r = bf / w;
+    ss = fmaf(r, r, ss);
   }
-  return false;
+  // the convergence control (norm, contraction rate) is FP32: it only decides when to stop
+  const float nrm = sqrtf(ss * (1.0f / NS));
+  if (!(nrm == nrm)) return -1;
+  if (it > 0) {
+    const float theta = nrm / prev;
+    if (theta >= 1.0f) {
+      // not contracting: accept only at the FP32 noise floor (below half the error weight)
+      return (nrm <= 0.5f && theta < 2.0f) ? 1 : -1;
+    }
+    eta = theta / (1.0f - theta);
+  }
+  if (eta * nrm <= static_cast<float>(kNewtTol) || nrm <= 1e-3f) return 1;
+  prev = nrm;
+  return ++it < kNewtMax ? 0 : -1;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Grid-wide barrier between the continuation rounds (the launch is cooperative, so every CTA is
+// resident).  The wait is bounded: after 4 s of wall time the CTA records kFlagStage and returns
+// false, and the kernel ends.
+__device__ bool grid_barrier(Workspace* ws) {
+  __shared__ int ok_s;
+  __threadfence();   // this thread's list entries and parked states, visible device-wide
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = &ws->bar_gen;
+    const unsigned g = *gen;
+    __threadfence();
+    int ok = 1;
+    if (atomicAdd(&ws->bar_count, 1u) == gridDim.x - 1) {
+      atomicExch(&ws->bar_count, 0u);
+      __threadfence();
+      atomicAdd(&ws->bar_gen, 1u);
+    } else {
+      const unsigned long long t0 = global_ns();
+      while (*gen == g) {
+        __nanosleep(256);
+        if (global_ns() - t0 > 4000000000ull) {
+          ok = 0;
+          atomicOr(&ws->status, kFlagStage);
+          break;
+        }
+      }
+    }
+    __threadfence();
+    ok_s = ok;
+  }
+  __syncthreads();
+  return ok_s != 0;
 }
 
 template <int NS, typename S>
@@ -211,12 +249,20 @@ __global__ void __launch_bounds__(kStiffBlock) stiff_kernel(const AdvanceArgs<S>
   sm.V = sm.M + NS * NS * kStiffBlock;
 
   const int lane = threadIdx.x & 31;
-  // probe and single passes take cells from the stiff queue; the continuation pass takes the
-  // queue slots the probe pass left unfinished, in their sorted order
+  // probe and single passes take cells from the stiff queue through an atomic head.  The
+  // continuation pass runs in rounds.  Round 0 takes the sorted unfinished cells from a shared
+  // queue (longest remaining first) and runs them to completion until the queue is empty; from
+  // then on a lane parks its cell after kRoundAttempts more steps.  Round r >= 1 gives every
+  // parked cell up to kRoundAttempts steps and lists those still unfinished for round r + 1; slot
+  // q of its list belongs to lane q % 32 of warp q / 32 mod W, warps numbered across the CTAs
+  // first, so that the cells still running fill whole warps spread over all SMs.
   const int pass = a.pass;
-  const int qn = pass == 2 ? min(*reinterpret_cast<volatile int*>(&a.ws->cont_count), static_cast<int>(a.n))
-                           : min(*reinterpret_cast<volatile int*>(&a.ws->qcount), static_cast<int>(a.n));
+  int qn = pass == 2 ? min(*reinterpret_cast<volatile int*>(&a.ws->cont_count), static_cast<int>(a.n))
+                     : min(*reinterpret_cast<volatile int*>(&a.ws->qcount), static_cast<int>(a.n));
   int* head = pass == 2 ? &a.ws->head2 : &a.ws->head;
+  // round r >= 1 reads cont_list (r odd) or cont_sorted (r even) and writes the other one;
+  // natt_r: steps in the round (round 0: steps since the queue ran empty, -1 before)
+  int round = 0, kr = 0, natt_r = 0;
   const long long cc = a.cont_cap;
   double* const cst = a.cont;   // continuation state, SoA by queue slot
   CellCtx c;
@@ -230,7 +276,7 @@ __global__ void __launch_bounds__(kStiffBlock) stiff_kernel(const AdvanceArgs<S>
   double y[NS], t = 0.0, h = 0.0, Tc = 0.0;
   float cvR = 1.0f;
   int nst = 0, natt = 0;
-  double eta_cell = 1.0;   // Newton contraction estimate carried from step to step
+  float eta_cell = 1.0f;   // Newton contraction estimate carried from step to step
   unsigned long long c_sub = 0, c_fail = 0, c_att = 0, c_newt = 0;
   int flags = 0;
 
@@ -239,32 +285,44 @@ __global__ void __launch_bounds__(kStiffBlock) stiff_kernel(const AdvanceArgs<S>
     const bool need = (cell < 0) && !done;
     const unsigned needm = __ballot_sync(0xffffffffu, need);
     if (needm) {
-      const int leader = __ffs(needm) - 1;
       int base = 0;
-      if (lane == leader) base = atomicAdd(head, __popc(needm));
-      base = __shfl_sync(0xffffffffu, base, leader);
+      if (pass != 2 || round == 0) {
+        const int leader = __ffs(needm) - 1;
+        if (lane == leader) base = atomicAdd(head, __popc(needm));
+        base = __shfl_sync(0xffffffffu, base, leader);
+      }
       if (need) {
-        const int q = base + __popc(needm & ((1u << lane) - 1u));
+        long long q;
+        if (pass == 2 && round > 0) {
+          const long long wg = static_cast<long long>(threadIdx.x >> 5) * gridDim.x + blockIdx.x;
+          q = (wg + static_cast<long long>(kr) * gridDim.x * (kStiffBlock / 32)) * 32 + lane;
+          ++kr;
+        } else {
+          q = base + __popc(needm & ((1u << lane) - 1u));
+        }
         if (q < qn) {
-          qpos = pass == 2 ? a.cont_sorted[q] : q;
+          natt_r = (pass == 2 && round == 0) ? -1 : 0;
+          // lists and parked states of the continuation rounds are written by other CTAs during
+          // this launch: read them past L1 (ld.global.cg)
+          qpos = pass == 2 ? __ldcg(((round & 1) ? a.cont_list : a.cont_sorted) + q) : static_cast<int>(q);
           cell = a.queue[qpos];
           const CellRef<S> cr = locate(a, soff, cell);
           const long long i = cr.i;
           dt = cr.dt;
           c.rho = static_cast<float>(cr.rho[i]);
           c.e0 = static_cast<double>(cr.e[i]);
-          if (pass == 2) {   // resume where the probe pass stopped
+          if (pass == 2) {   // resume where the previous pass or round stopped
 #pragma unroll
-            for (int k = 0; k < NS; ++k) y[k] = cst[k * cc + qpos];
-            t = cst[NS * cc + qpos];
-            h = cst[(NS + 1) * cc + qpos];
-            Tc = cst[(NS + 2) * cc + qpos];
-            eta_cell = cst[(NS + 3) * cc + qpos];
+            for (int k = 0; k < NS; ++k) y[k] = __ldcg(cst + k * cc + qpos);
+            t = __ldcg(cst + NS * cc + qpos);
+            h = __ldcg(cst + (NS + 1) * cc + qpos);
+            Tc = __ldcg(cst + (NS + 2) * cc + qpos);
+            eta_cell = static_cast<float>(__ldcg(cst + (NS + 3) * cc + qpos));
             const float* cf = reinterpret_cast<const float*>(cst + (NS + 4) * cc);
             const int* ci = reinterpret_cast<const int*>(cf + cc);
-            cvR = cf[qpos];
-            nst = ci[qpos];
-            natt = ci[cc + qpos];
+            cvR = __ldcg(cf + qpos);
+            nst = __ldcg(ci + qpos);
+            natt = __ldcg(ci + cc + qpos);
           } else {
 #pragma unroll
             for (int k = 0; k < NS; ++k) y[k] = static_cast<double>(cr.Y[k * cr.ld + i]);
@@ -276,7 +334,7 @@ __global__ void __launch_bounds__(kStiffBlock) stiff_kernel(const AdvanceArgs<S>
             nst = 0;
             natt = 0;
             h = 1e-6 * dt;   // the controller grows it by up to 5x per accepted step
-            eta_cell = 1.0;
+            eta_cell = 1.0f;
             if (!ok) {       // temperature not invertible: fail the cell right away
               cr.sub[i] = -1;
               ++c_fail;
@@ -289,12 +347,29 @@ __global__ void __launch_bounds__(kStiffBlock) stiff_kernel(const AdvanceArgs<S>
         }
       }
     }
-    if (__all_sync(0xffffffffu, cell < 0)) break;
+    if (__all_sync(0xffffffffu, cell < 0)) {
+      if (pass != 2) break;
+      // end of a continuation round: wait for every CTA, then take the survivors' list
+      if (!grid_barrier(a.ws)) break;
+      const int next = min(*reinterpret_cast<volatile int*>(&a.ws->rc[round % 3]), static_cast<int>(a.n));
+      if (next == 0) break;
+      ++round;
+      if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(&a.ws->rc[(round + 1) % 3], 0);   // output of round + 1
+      qn = next;
+      kr = 0;
+      done = false;
+      continue;
+    }
+    const unsigned work = __ballot_sync(0xffffffffu, cell >= 0);   // the lanes that take a step
     if (cell < 0) continue;
 
     // ---- one attempted SDIRK3 step for this lane's cell
     ++natt;
     ++c_att;
+    if (pass == 2) {
+      if (natt_r < 0 && *reinterpret_cast<volatile const int*>(head) >= qn) natt_r = 0;   // queue empty
+      if (natt_r >= 0) ++natt_r;
+    }
     const double gh = kG * h;
     uint64_t piv;
     bool conv;
@@ -307,41 +382,66 @@ __global__ void __launch_bounds__(kStiffBlock) stiff_kernel(const AdvanceArgs<S>
       store_iteration_matrix<NS>(sm, J, gh);
     }
     conv = lu_factor<NS>(sm, &piv);
-    // stage s solves Y_s = y + sum_j A_sj hk_j + g h f(Y_s), hk_j = h k_j, starting from
-    // y + sum_j P_sj hk_j (extrapolation of the previous stages to c_s)
     double hk1[NS], hk2[NS], z[NS], base[NS];
     double Tz = Tc;
-    double eta = eta_cell;
+    float eta = eta_cell;
 #pragma unroll
     for (int k = 0; k < NS; ++k) {
       hk1[k] = 0.0;
       hk2[k] = 0.0;
     }
+    // the three stages run as one flat sequence of Newton iterations per lane, so that a lane
+    // whose stage converges early starts its next stage instead of waiting for the slowest lane:
+    // the warp pays max over lanes of the step's iterations rather than the sum over stages of
+    // the per-stage maxima.  Stage s solves Y_s = y + sum_j A_sj hk_j + g h f(Y_s), hk_j = h k_j,
+    // starting from y + sum_j P_sj hk_j (extrapolation of the previous stages to c_s).
+    int st = 0, it = 0;
+    float prev = 0.0f;
+    bool act = conv;
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+      base[k] = y[k];
+      z[k] = y[k];
+    }
 #pragma unroll 1
-    for (int st = 0; st < 3 && conv; ++st) {
-      const double a1 = st == 1 ? kA21 : (st == 2 ? kB1 : 0.0);
-      const double a2 = st == 2 ? kB2 : 0.0;
-      const double p1 = st == 1 ? kC2 : (st == 2 ? kA21 / kC2 : 0.0);
-      const double p2 = st == 2 ? kG / kC2 : 0.0;
+    while (__any_sync(work, act)) {
+      if (act) {
+        const int r = newton_iteration<NS>(m, sm, piv, c, base, gh, z, Tz, eta, prev, it, c_newt);
+        if (r < 0) {
+          conv = false;
+          act = false;
+        } else if (r > 0) {
+          if (st < 2) {
 #pragma unroll
-      for (int k = 0; k < NS; ++k) {
-        base[k] = y[k] + a1 * hk1[k] + a2 * hk2[k];
-        z[k] = y[k] + p1 * hk1[k] + p2 * hk2[k];
-      }
-      conv = stage_newton<NS>(m, sm, piv, c, base, gh, z, Tz, eta, c_newt);
-      if (st < 2) {
+            for (int k = 0; k < NS; ++k) {
+              const double hk = (z[k] - base[k]) * (1.0 / kG);
+              if (st == 0) hk1[k] = hk; else hk2[k] = hk;
+            }
+          }
+          ++st;
+          if (st == 3) {
+            act = false;
+          } else {
+            const double a1 = st == 1 ? kA21 : kB1;
+            const double a2 = st == 2 ? kB2 : 0.0;
+            const double p1 = st == 1 ? kC2 : kA21 / kC2;
+            const double p2 = st == 2 ? kG / kC2 : 0.0;
 #pragma unroll
-        for (int k = 0; k < NS; ++k) {
-          const double hk = (z[k] - base[k]) * (1.0 / kG);
-          if (st == 0) hk1[k] = hk; else hk2[k] = hk;
+            for (int k = 0; k < NS; ++k) {
+              base[k] = y[k] + a1 * hk1[k] + a2 * hk2[k];
+              z[k] = y[k] + p1 * hk1[k] + p2 * hk2[k];
+            }
+            it = 0;
+            prev = 0.0f;
+          }
         }
       }
     }
-    eta_cell = fmax(eta, 0.05);
+    eta_cell = fmaxf(eta, 0.05f);
     bool finished = false, failed = false;
     if (!conv) {
       h *= 0.25;
-      eta_cell = 1.0;
+      eta_cell = 1.0f;
     } else {
       // y_new = Y3 (stiffly accurate); error = (b - bh) . hk, filtered through (I - g h J)^-1
       double er[NS];
@@ -351,18 +451,20 @@ __global__ void __launch_bounds__(kStiffBlock) stiff_kernel(const AdvanceArgs<S>
         er[k] = (kB1 - kBh1) * hk1[k] + (kB2 - kBh2) * hk2[k] + kG * hk3;
       }
       lu_solve<NS>(sm, piv, er);
-      double err = 0.0;
+      // the weighted error norm is a step-size control quantity: FP32
+      float err = 0.0f;
       bool neg = false;
 #pragma unroll
       for (int k = 0; k < NS; ++k) {
-        const double w = static_cast<double>(c.atol) + static_cast<double>(c.rtol) * fmax(fabs(y[k]), fabs(z[k]));
-        err = fmax(err, fabs(er[k]) / w);
-        neg = neg || z[k] < -10.0 * static_cast<double>(c.atol);
+        const float zk = static_cast<float>(z[k]);
+        const float w = c.atol + c.rtol * fmaxf(fabsf(static_cast<float>(y[k])), fabsf(zk));
+        err = fmaxf(err, fabsf(static_cast<float>(er[k])) / w);
+        neg = neg || zk < -10.0f * c.atol;
       }
       // a solution with a clearly negative mass fraction is rejected: an overshoot that the main
       // and the embedded solution share is invisible to the error estimate
-      if (neg) err = fmax(err, 4.0);
-      if (err <= 1.0) {
+      if (neg) err = fmaxf(err, 4.0f);
+      if (err <= 1.0f) {
         bool ok;
         double cvd;
         const double Tn = temperature_from_energy<NS>(m, z, c.e0, Tz, &ok, &cvd);
@@ -375,36 +477,42 @@ __global__ void __launch_bounds__(kStiffBlock) stiff_kernel(const AdvanceArgs<S>
           ++nst;
           if (t >= dt * (1.0 - 1e-12)) finished = true;
         } else {
-          err = 4.0;   // treat as a rejected step
+          err = 4.0f;   // treat as a rejected step
         }
       }
-      double fac = 0.9 * rcbrt(fmax(err, 1e-12));   // embedded order 2: error ~ h^3
-      fac = fmin(5.0, fmax(0.2, fac));
-      h *= fac;
+      float fac = 0.9f * rcbrtf(fmaxf(err, 1e-12f));   // embedded order 2: error ~ h^3
+      fac = fminf(5.0f, fmaxf(0.2f, fac));
+      h *= static_cast<double>(fac);
     }
     if (!finished) {
       if (t + h > dt) h = dt - t;
       if (h < 1e-24 * dt || h < 1e-30) { failed = true; flags |= kFlagNoConv; }
       if (nst >= a.prm.k_max || natt >= 4 * a.prm.k_max) { failed = true; flags |= kFlagMaxSteps; }
     }
-    if (!finished && !failed && pass == 1 && natt >= kProbeAttempts) {
-      // probe pass: park the cell with its integration state and the remaining-work estimate
+    if (!finished && !failed &&
+        ((pass == 1 && natt >= kProbeAttempts) || (pass == 2 && natt_r >= kRoundAttempts))) {
+      // park the cell with its integration state (probe pass: for the sort and round 0; later:
+      // for the next round)
 #pragma unroll
       for (int k = 0; k < NS; ++k) cst[k * cc + qpos] = y[k];
       cst[NS * cc + qpos] = t;
       cst[(NS + 1) * cc + qpos] = h;
       cst[(NS + 2) * cc + qpos] = Tc;
-      cst[(NS + 3) * cc + qpos] = eta_cell;
+      cst[(NS + 3) * cc + qpos] = static_cast<double>(eta_cell);
       float* cf = reinterpret_cast<float*>(cst + (NS + 4) * cc);
       int* ci = reinterpret_cast<int*>(cf + cc);
       cf[qpos] = cvR;
       ci[qpos] = nst;
       ci[cc + qpos] = natt;
-      const int pos = atomicAdd(&a.ws->cont_count, 1);
-      a.cont_list[pos] = qpos;
-      const float rest = static_cast<float>((dt - t) / h);   // steps left at the current step size
-      a.cont_key[pos] = static_cast<unsigned char>(fminf(fmaxf(4.0f * __log2f(rest + 1.0f), 0.0f),
-                                                         static_cast<float>(kNumBuckets - 1)));
+      if (pass == 1) {
+        const int pos = atomicAdd(&a.ws->cont_count, 1);
+        a.cont_list[pos] = qpos;
+        const float rest = static_cast<float>((dt - t) / h);   // steps left at the current step size
+        a.cont_key[pos] = static_cast<unsigned char>(fminf(fmaxf(4.0f * __log2f(rest + 1.0f), 0.0f),
+                                                           static_cast<float>(kNumBuckets - 1)));
+      } else {
+        ((round & 1) ? a.cont_sorted : a.cont_list)[atomicAdd(&a.ws->rc[round % 3], 1)] = qpos;
+      }
       cell = -1;
     }
     if (finished) {
@@ -460,6 +568,19 @@ static int stiff_launch_t(const AdvanceArgs<S>& a, int grid, cudaStream_t s) {
   const size_t smem = stiff_smem_bytes(NS, a.blob_bytes, a.nbox);
   auto k = stiff_kernel<NS, S>;
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  if (a.pass == 2) {   // continuation rounds: grid barriers need every CTA resident
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kStiffBlock);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return static_cast<int>(cudaLaunchKernelEx(&cfg, k, a, pad128(a.blob_bytes)));
+  }
   k<<<grid, kStiffBlock, smem, s>>>(a, pad128(a.blob_bytes));
   return static_cast<int>(cudaGetLastError());
 }

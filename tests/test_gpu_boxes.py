@@ -96,6 +96,24 @@ def test_boxes_match_per_box_advance_oracle_and_graph(h2mech):
         assert st2["status"] == 0 and st2["nqueued"] == st["nqueued"]
         for (T1, Y1), d in zip(direct, dev):
             assert torch.equal(T1, d["T"]) and torch.equal(Y1, d["Y"])
+    # the two-pass schedule (probe launch, then a cooperative launch of continuation rounds) in a
+    # captured graph gives the same bits
+    ctx.set_params(flags=ctx.params.flags | chem.CHEM_FLAG_TWO_PASS)
+    with torch.cuda.stream(stream):
+        for d, b in zip(dev, boxes):
+            d["T"].copy_(torch.from_numpy(b["T"]))
+            d["Y"].copy_(torch.from_numpy(b["Y"]))
+    torch.cuda.synchronize()
+    ctx.capture_boxes(stream)
+    with torch.cuda.stream(stream):
+        for d, b in zip(dev, boxes):
+            d["T"].copy_(torch.from_numpy(b["T"]))
+            d["Y"].copy_(torch.from_numpy(b["Y"]))
+    ctx.launch_boxes(stream)
+    st3 = ctx.status(stream)
+    assert st3["status"] == 0 and st3["nqueued"] == st["nqueued"] and st3["attempts"] == st["attempts"]
+    for (T1, Y1), d in zip(direct, dev):
+        assert torch.equal(T1, d["T"]) and torch.equal(Y1, d["Y"])
     ctx.close()
 
 
