@@ -96,6 +96,17 @@ int pack_mechanism(const chem_mechanism* m, std::vector<unsigned char>& out, int
   h.nsp = nsp;
   h.large = large ? 1 : 0;
   h.nnz = nnz;
+  // trailing species that no reaction changes (a bath gas such as N2): the stiff kernel leaves
+  // them out of the Newton linear algebra, where their rows are those of the identity
+  int nact = ns;
+  while (nact > 1) {
+    bool inert = true;
+    for (int r = 0; r < nr && inert; ++r) inert = m->nu_r[r * ns + nact - 1] == m->nu_f[r * ns + nact - 1];
+    if (!inert) break;
+    --nact;
+  }
+  h.nact = nact;
+
   const double T_lo = m->thermo[7], T_hi = m->thermo[8];
   h.T_lo = static_cast<float>(T_lo);
   h.T_hi = static_cast<float>(T_hi);

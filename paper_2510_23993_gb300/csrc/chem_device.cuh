@@ -29,7 +29,9 @@ enum : int { kFlagInvalid = 1, kFlagMaxSteps = 2, kFlagNoConv = 4, kFlagStage = 
 // Layout of the packed mechanism blob (byte offsets, all multiples of 16).
 struct MechHdr {
   int ns, nr, ntb, nsp;          // nsp = ns rounded up to 4
-  float T_lo, T_hi, lnP0R, pad1; // lnP0R = ln(p0 / R)
+  float T_lo, T_hi, lnP0R;       // lnP0R = ln(p0 / R)
+  int nact;                      // species before the trailing run of inert ones (no net
+                                 //   stoichiometry in any reaction); 0 = all species
   int off_arr, off_nuf, off_nur, off_dnu;
   int off_eff, off_rinfo, off_W, off_invW;
   int off_gam, off_hco, off_hsp, off_e64;
@@ -43,7 +45,7 @@ struct MechHdr {
 
 // Device view of the (staged) tables.
 struct MechView {
-  int ns, nr, nsp;
+  int ns, nr, nsp, nact;
   float T_lo, T_hi, lnP0R;
   const float4* arr;     // [nr] lnA, b, Ea/R, sum dnu
   const float* nuf;      // [nr][nsp]
@@ -68,6 +70,7 @@ __device__ __forceinline__ MechView make_view(const unsigned char* base) {
   v.ns = h->ns;
   v.nr = h->nr;
   v.nsp = h->nsp;
+  v.nact = h->nact > 0 ? h->nact : h->ns;
   v.T_lo = h->T_lo;
   v.T_hi = h->T_hi;
   v.lnP0R = h->lnP0R;

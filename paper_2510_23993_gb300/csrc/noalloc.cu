@@ -89,6 +89,15 @@ unsigned pack_into(const chem_mechanism* m, unsigned char* out, size_t cap) {
   h.nr = nr;
   h.ntb = ntb;
   h.nsp = nsp;
+  // trailing species that no reaction changes: left out of the stiff kernel's linear algebra
+  int nact = ns;
+  while (nact > 1) {
+    bool inert = true;
+    for (int r = 0; r < nr && inert; ++r) inert = m->nu_r[r * ns + nact - 1] == m->nu_f[r * ns + nact - 1];
+    if (!inert) break;
+    --nact;
+  }
+  h.nact = nact;
   const double T_lo = m->thermo[7], T_hi = m->thermo[8];
   h.T_lo = static_cast<float>(T_lo);
   h.T_hi = static_cast<float>(T_hi);

@@ -50,28 +50,34 @@ struct Smem {
 // hh * J is formed in FP32: J carries FP32 rounding already, so the FP64 product would add no
 // accuracy, and it saves NS^2 FP64 multiplies per attempt; the identity is added in FP64.
 template <int NS>
-__device__ __forceinline__ void store_iteration_matrix(const Smem<NS>& s, const float (&J)[NS][NS], double hh) {
+__device__ __forceinline__ void store_iteration_matrix(const Smem<NS>& s, const float (&J)[NS][NS], double hh,
+                                                       int na) {
   const float mh = static_cast<float>(-hh);
 #pragma unroll
   for (int r = 0; r < NS; ++r)
 #pragma unroll
     for (int c = 0; c < NS; ++c) {
-      const double v = static_cast<double>(mh * J[r][c]);
-      s.mm(r, c) = r == c ? 1.0 + v : v;
+      if (r < na && c < na) {
+        const double v = static_cast<double>(mh * J[r][c]);
+        s.mm(r, c) = r == c ? 1.0 + v : v;
+      }
     }
 }
 
 // LU with partial pivoting in place (unit-lower L below the diagonal, U above, reciprocal of
-// U's diagonal on it); pivot rows packed 4 bits each into *piv.
+// U's diagonal on it); pivot rows packed 4 bits each into *piv.  Only the leading na x na block
+// is factored: the rows of the trailing inert species are rows of the identity (their rates
+// vanish identically), so with a zero right-hand side there the solution of the full system
+// is the block's solution extended by zeros, bit for bit.
 template <int NS>
-__device__ __forceinline__ bool lu_factor(const Smem<NS>& s, uint64_t* piv) {
+__device__ __forceinline__ bool lu_factor(const Smem<NS>& s, uint64_t* piv, int na) {
   uint64_t pv = 0;
 #pragma unroll 1
-  for (int k = 0; k < NS; ++k) {
+  for (int k = 0; k < na; ++k) {
     int p = k;
     double best = fabs(s.mm(k, k));
 #pragma unroll 1
-    for (int i = k + 1; i < NS; ++i) {
+    for (int i = k + 1; i < na; ++i) {
       const double v = fabs(s.mm(i, k));
       if (v > best) {
         best = v;
@@ -82,7 +88,7 @@ __device__ __forceinline__ bool lu_factor(const Smem<NS>& s, uint64_t* piv) {
     pv |= static_cast<uint64_t>(p) << (4 * k);
     if (p != k) {
 #pragma unroll 1
-      for (int c = 0; c < NS; ++c) {
+      for (int c = 0; c < na; ++c) {
         const double t = s.mm(k, c);
         s.mm(k, c) = s.mm(p, c);
         s.mm(p, c) = t;
@@ -91,11 +97,11 @@ __device__ __forceinline__ bool lu_factor(const Smem<NS>& s, uint64_t* piv) {
     const double inv = 1.0 / s.mm(k, k);
     s.mm(k, k) = inv;
 #pragma unroll 1
-    for (int i = k + 1; i < NS; ++i) {
+    for (int i = k + 1; i < na; ++i) {
       const double l = s.mm(i, k) * inv;
       s.mm(i, k) = l;
 #pragma unroll 2
-      for (int c = k + 1; c < NS; ++c) s.mm(i, c) = fma(-l, s.mm(k, c), s.mm(i, c));
+      for (int c = k + 1; c < na; ++c) s.mm(i, c) = fma(-l, s.mm(k, c), s.mm(i, c));
     }
   }
   *piv = pv;
@@ -103,13 +109,14 @@ __device__ __forceinline__ bool lu_factor(const Smem<NS>& s, uint64_t* piv) {
 }
 
 // Solve M x = b with the factors of lu_factor (b in registers, in and out; the permutation and
-// the substitutions run on the shared-memory vector).
+// the substitutions run on the shared-memory vector).  Entries na.. of b (the inert species,
+// zero) pass through unchanged.
 template <int NS>
-__device__ __forceinline__ void lu_solve(const Smem<NS>& s, uint64_t piv, double (&b)[NS]) {
+__device__ __forceinline__ void lu_solve(const Smem<NS>& s, uint64_t piv, double (&b)[NS], int na) {
 #pragma unroll
   for (int k = 0; k < NS; ++k) s.vv(k) = b[k];
 #pragma unroll 1
-  for (int k = 0; k < NS; ++k) {
+  for (int k = 0; k < na; ++k) {
     const int p = static_cast<int>((piv >> (4 * k)) & 15u);
     if (p != k) {
       const double t = s.vv(k);
@@ -118,17 +125,17 @@ __device__ __forceinline__ void lu_solve(const Smem<NS>& s, uint64_t piv, double
     }
   }
 #pragma unroll 1
-  for (int i = 1; i < NS; ++i) {
+  for (int i = 1; i < na; ++i) {
     double acc = s.vv(i);
 #pragma unroll 1
     for (int j = 0; j < i; ++j) acc = fma(-s.mm(i, j), s.vv(j), acc);
     s.vv(i) = acc;
   }
 #pragma unroll 1
-  for (int i = NS - 1; i >= 0; --i) {
+  for (int i = na - 1; i >= 0; --i) {
     double acc = s.vv(i);
 #pragma unroll 1
-    for (int j = i + 1; j < NS; ++j) acc = fma(-s.mm(i, j), s.vv(j), acc);
+    for (int j = i + 1; j < na; ++j) acc = fma(-s.mm(i, j), s.vv(j), acc);
     s.vv(i) = acc * s.mm(i, i);
   }
 #pragma unroll
@@ -168,7 +175,7 @@ __device__ __forceinline__ int newton_iteration(const MechView& m, const Smem<NS
   double b[NS];
 #pragma unroll
   for (int k = 0; k < NS; ++k) b[k] = (yb[k] - z[k]) + static_cast<double>(mhh * F[k]);
-  lu_solve<NS>(s, piv, b);
+  lu_solve<NS>(s, piv, b, m.nact);
   float ss = 0.0f;
 #pragma unroll
   for (int k = 0; k < NS; ++k) {
@@ -379,9 +386,9 @@ __global__ void __launch_bounds__(kStiffBlock) stiff_kernel(const AdvanceArgs<S>
       for (int k = 0; k < NS; ++k) Yf[k] = static_cast<float>(y[k]);
       float J[NS][NS];
       jacobian<NS>(m, c.rho, static_cast<float>(Tc), Yf, cvR, J);
-      store_iteration_matrix<NS>(sm, J, gh);
+      store_iteration_matrix<NS>(sm, J, gh, m.nact);
     }
-    conv = lu_factor<NS>(sm, &piv);
+    conv = lu_factor<NS>(sm, &piv, m.nact);
     double hk1[NS], hk2[NS], z[NS], base[NS];
     double Tz = Tc;
     float eta = eta_cell;
@@ -450,7 +457,7 @@ __global__ void __launch_bounds__(kStiffBlock) stiff_kernel(const AdvanceArgs<S>
         const double hk3 = (z[k] - base[k]) * (1.0 / kG);
         er[k] = (kB1 - kBh1) * hk1[k] + (kB2 - kBh2) * hk2[k] + kG * hk3;
       }
-      lu_solve<NS>(sm, piv, er);
+      lu_solve<NS>(sm, piv, er, m.nact);
       // the weighted error norm is a step-size control quantity: FP32
       float err = 0.0f;
       bool neg = false;
