@@ -1,6 +1,6 @@
 """GPU parity of the CUDA path (through the C ABI) against the FP64 CPU oracle.
 
-Tolerances (the task's accuracy target; the derivations are in the design doc):
+Tolerances (the accuracy target: 1e-4 relative on T and on every non-negligible Y):
   * advanced state: |T - T_ref| / T_ref <= 1e-4; Y_ref >= 1e-6: |Y - Y_ref| / Y_ref <= 1e-4;
     Y_ref < 1e-6: |Y - Y_ref| <= 1e-10.  This bar is applied as is to the FP64-rate mode and to
     every well-conditioned cell.  The default mode evaluates rates from FP32-rounded tables,
