@@ -456,10 +456,23 @@ __device__ bool warp_lu(const Scratch& s) {
     const double inv = 1.0 / M[k * NS + k];
     for (int i = k + 1 + lane; i < NS; i += 32) M[i * NS + k] *= inv;
     __syncwarp();
-    for (int c = k + 1 + lane; c < NS; c += 32) {
-      const double ukc = M[k * NS + c];
-#pragma unroll 4
-      for (int i = k + 1; i < NS; ++i) M[i * NS + c] = fma(-M[i * NS + k], ukc, M[i * NS + c]);
+    // rank-1 update of the trailing m x m block, spread over the lanes element by element
+    // (row-major order), so that all 32 lanes work until the block is smaller than the warp;
+    // every element takes the same single FMA as in a column-per-lane sweep
+    if (k < NS - 1) {
+      const int m = NS - 1 - k;
+      const int q = 32 / m, r = 32 - q * m;   // a stride of 32 elements: q rows and r columns
+      int ii = lane / m, cc = lane - (lane / m) * m;
+      for (int e = lane; e < m * m; e += 32) {
+        const int i = k + 1 + ii, c = k + 1 + cc;
+        M[i * NS + c] = fma(-M[i * NS + k], M[k * NS + c], M[i * NS + c]);
+        ii += q;
+        cc += r;
+        if (cc >= m) {
+          cc -= m;
+          ++ii;
+        }
+      }
     }
     __syncwarp();
     if (lane == 0) M[k * NS + k] = inv;
