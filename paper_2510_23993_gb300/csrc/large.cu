@@ -417,12 +417,15 @@ __device__ __forceinline__ void warp_iteration_matrix(const Scratch& s, double h
   __syncwarp();
 }
 
-// LU with partial pivoting by the warp (unit-lower L, U with its diagonal inverted; pivots in
-// s.piv).  Returns false (warp-uniform) for a singular matrix.
+// LU with partial pivoting by the warp (unit-lower L, U with its diagonal inverted; s.piv holds
+// the composite row permutation: row k of the factors is row s.piv[k] of the original matrix).
+// Returns false (warp-uniform) for a singular matrix.
 template <int NS>
 __device__ bool warp_lu(const Scratch& s) {
   const int lane = threadIdx.x & 31;
   double* M = s.M;
+  for (int i = lane; i < NS; i += 32) s.piv[i] = i;
+  __syncwarp();
 #pragma unroll 1
   for (int k = 0; k < NS; ++k) {
     double best = -1.0;
@@ -444,8 +447,12 @@ __device__ bool warp_lu(const Scratch& s) {
       }
     }
     if (!(best > 0.0)) return false;
-    if (lane == 0) s.piv[k] = p;
     if (p != k) {
+      if (lane == 0) {
+        const int t = s.piv[k];
+        s.piv[k] = s.piv[p];
+        s.piv[p] = t;
+      }
       for (int c = lane; c < NS; c += 32) {
         const double t = M[k * NS + c];
         M[k * NS + c] = M[p * NS + c];
@@ -481,9 +488,13 @@ __device__ bool warp_lu(const Scratch& s) {
   return true;
 }
 
-// x = M^-1 b with the factors of warp_lu; b / x: this lane's entries lane and lane + 32
+// x = M^-1 b with the factors of warp_lu; b / x: this lane's entries lane and lane + 32.  The
+// permuted right-hand side is gathered through shared memory once; the substitutions then keep
+// x in registers (lane-owned entries) and broadcast each finished entry with a shuffle, in the
+// same order of operations per entry as a column sweep.
 template <int NS>
 __device__ void warp_solve(const Scratch& s, double (&b)[2]) {
+  static_assert(NS <= 64, "two entries per lane");
   const int lane = threadIdx.x & 31;
   const double* M = s.M;
   double* v = s.v;
@@ -493,37 +504,30 @@ __device__ void warp_solve(const Scratch& s, double (&b)[2]) {
     if (k < NS) v[k] = b[kk];
   }
   __syncwarp();
-  if (lane == 0) {
-    for (int k = 0; k < NS; ++k) {
-      const int p = s.piv[k];
-      if (p != k) {
-        const double t = v[k];
-        v[k] = v[p];
-        v[p] = t;
-      }
-    }
-  }
-  __syncwarp();
-#pragma unroll 1
-  for (int j = 0; j < NS - 1; ++j) {
-    const double vj = v[j];
-    for (int i = j + 1 + lane; i < NS; i += 32) v[i] = fma(-M[i * NS + j], vj, v[i]);
-    __syncwarp();
-  }
-#pragma unroll 1
-  for (int j = NS - 1; j >= 0; --j) {
-    const double vj = v[j] * M[j * NS + j];
-    __syncwarp();
-    if (lane == 0) v[j] = vj;
-    for (int i = lane; i < j; i += 32) v[i] = fma(-M[i * NS + j], vj, v[i]);
-    __syncwarp();
-  }
+  double x[2];
 #pragma unroll
   for (int kk = 0; kk < 2; ++kk) {
     const int k = lane + 32 * kk;
-    b[kk] = k < NS ? v[k] : 0.0;
+    x[kk] = k < NS ? v[s.piv[k]] : 0.0;
   }
   __syncwarp();
+  const int i0 = lane, i1 = lane + 32;
+#pragma unroll 1
+  for (int j = 0; j < NS - 1; ++j) {
+    const double vj = __shfl_sync(0xffffffffu, j < 32 ? x[0] : x[1], j & 31);
+    if (i0 > j) x[0] = fma(-M[i0 * NS + j], vj, x[0]);
+    if (i1 > j && i1 < NS) x[1] = fma(-M[i1 * NS + j], vj, x[1]);
+  }
+#pragma unroll 1
+  for (int j = NS - 1; j >= 0; --j) {
+    if (i0 == j) x[0] *= M[j * NS + j];
+    if (i1 == j) x[1] *= M[j * NS + j];
+    const double vj = __shfl_sync(0xffffffffu, j < 32 ? x[0] : x[1], j & 31);
+    if (i0 < j) x[0] = fma(-M[i0 * NS + j], vj, x[0]);
+    if (i1 < j) x[1] = fma(-M[i1 * NS + j], vj, x[1]);
+  }
+  b[0] = x[0];
+  b[1] = i1 < NS ? x[1] : 0.0;
 }
 
 struct CellCtx {
