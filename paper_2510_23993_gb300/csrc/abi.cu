@@ -60,10 +60,6 @@ struct chem_ctx {
   double* xcell = nullptr;
 };
 
-namespace chem {
-int occupancy_stiff(const chem_ctx* c);
-}
-
 namespace {
 
 int cuda_fail(cudaError_t e, const char* what) {
@@ -357,12 +353,8 @@ int launch_stiff_phase(chem_ctx* c, AdvanceArgs<S> b, long long n, cudaStream_t 
   b.pass = 1;
   int r = launch(b);
   if (!r) r = launch_order_queue(c->ws, c->cont_list, c->cont_key, c->cont_sorted, n, st, true);
-  b.pass = 2;   // cooperative: every CTA of the grid must be resident at once
-  const int coop = c->sms * occupancy_stiff(c);
-  if (!r) {
-    if constexpr (sizeof(S) == 4) r = launch_stiff_f32(c->ns, b, c->stiff_grid < coop ? c->stiff_grid : coop, st);
-    else r = launch_stiff_f64(c->ns, b, c->stiff_grid < coop ? c->stiff_grid : coop, st);
-  }
+  b.pass = 2;   // cooperative launch (its grid is capped at the CTAs that fit at once)
+  if (!r) r = launch(b);
   return r;
 }
 

@@ -576,6 +576,14 @@ static int stiff_launch_t(const AdvanceArgs<S>& a, int grid, cudaStream_t s) {
   auto k = stiff_kernel<NS, S>;
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (a.pass == 2) {   // continuation rounds: grid barriers need every CTA resident
+    // at most the CTAs that fit at once for this instantiation and shared-memory size (box
+    // offsets included)
+    int bps = 0, dev = 0, sms = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k, kStiffBlock, smem);
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long fit = static_cast<long long>(bps > 0 ? bps : 1) * (sms > 0 ? sms : 1);
+    if (grid > fit) grid = static_cast<int>(fit);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(kStiffBlock);

@@ -160,3 +160,32 @@ def test_full_size_400_boxes_sampled(h2mech):
         assert np.all(eY <= np.where(big, 1e-4, 1e-10) + 3 * dY)
         assert abs(To - T_ref[0]) / T_ref[0] <= 1e-4 + 3 * abs(T_p[0] - T_ref[0]) / T_ref[0]
     ctx.close()
+
+
+def test_two_pass_with_4000_boxes(h2mech):
+    """4000 small boxes: their offsets take 16 KB of shared memory per CTA, so fewer CTAs fit an
+    SM; the cooperative continuation launch still runs (its grid is capped at what fits) and
+    gives the bits of the single-pass schedule."""
+    rng = np.random.default_rng(4)
+    T, p, Y, hot = synth.sheet_field(h2mech, n=20, seed=12, frac=0.08)
+    T, p, Y = T.astype(np.float32), p.astype(np.float32), np.ascontiguousarray(Y, dtype=np.float32)
+    rho, e = oracle.state_from_TpY(h2mech, T, p, Y)
+    n = T.size
+    cuts = np.sort(rng.choice(np.arange(1, n), 3999, replace=False))
+    off = np.concatenate([[0], cuts, [n]])
+    res = []
+    for flags in (chem.CHEM_FLAG_ORDER_RATE, chem.CHEM_FLAG_ORDER_RATE | chem.CHEM_FLAG_TWO_PASS):
+        ctx = chem.Context(h2mech, max_cells=n, flags=flags)
+        tT, tp, tY, trho, te = (torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+                                for a in (T, p, Y, rho.astype(np.float32), e.astype(np.float32)))
+        sub = torch.zeros(n, dtype=torch.int32, device=DEV)
+        boxes = [dict(T=tT[a:b], p=tp[a:b], Y=tY[:, a:b], rho=trho[a:b], e=te[a:b], substeps=sub[a:b], dt=1e-8,
+                      level=0) for a, b in zip(off[:-1], off[1:])]
+        ctx.set_boxes(boxes)
+        ctx.advance_boxes()
+        st = ctx.status()
+        assert st["status"] == 0 and st["ncell"] == n
+        res.append((tT.cpu().numpy(), tY.cpu().numpy(), sub.cpu().numpy()))
+        ctx.close()
+    for a, b in zip(res[0], res[1]):
+        assert np.array_equal(a, b)

@@ -290,6 +290,23 @@ def test_two_pass_equals_single_pass(h2mech, order):
     ctx.close()
 
 
+def test_two_pass_equals_single_pass_f64_state(h2mech):
+    """The same with FP64 state arrays (chem_advance_f64): the FP64 instantiation of the
+    cooperative continuation launch sizes its grid for its own register use."""
+    T, p, Y, hot = synth.sheet_field(h2mech, n=16, seed=11, frac=0.08)
+    T, p, Y = T.astype(np.float64), p.astype(np.float64), np.ascontiguousarray(Y, dtype=np.float64)
+    rho, e = oracle.state_from_TpY(h2mech, T, p, Y)
+    ctx = chem.Context(h2mech, max_cells=T.size)
+    outs = []
+    for flags in (chem.CHEM_FLAG_ORDER_RATE, chem.CHEM_FLAG_ORDER_RATE | chem.CHEM_FLAG_TWO_PASS):
+        ctx.set_params(flags=flags)
+        outs.append(_run(ctx, T, p, Y, rho, e, 1e-8))
+    (rc1, st1, T1, p1, Y1, s1), (rc2, st2, T2, p2, Y2, s2) = outs
+    assert rc1 == 0 and rc2 == 0 and st2["status"] == 0 and (s1 > 1 + 32).sum() > 5
+    assert np.array_equal(T1, T2) and np.array_equal(Y1, Y2) and np.array_equal(s1, s2)
+    ctx.close()
+
+
 def test_host_entry_point_matches_device(h2mech):
     T, p, Y, hot = synth.sheet_field(h2mech, n=10, seed=8)
     T, p, Y, rho, e = _inputs32(h2mech, T, p, Y)
