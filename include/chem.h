@@ -190,7 +190,8 @@ int chem_advance_explicit(chem_ctx *ctx, float *T, float *p, float *Y, int64_t l
  * third-body rows), a cells x reactions kernel for the rates of progress, and a final SGEMM
  * q . (dnu W) that writes dY/dt.  Same inputs, output and precision (FP32) as chem_rates; kept
  * as the comparison point of the single-kernel strategy, per grid.  chem_mk_create copies the
- * mechanism, opens cuBLAS at run time (CHEM_EUNSUPPORTED if libcublas cannot be loaded) and
+ * mechanism, opens cuBLAS at run time (CHEM_EUNSUPPORTED if libcublas cannot be loaded or the
+ * mechanism has more than 65535 reactions) and
  * allocates 4 * (2 ns + 2 nr + ntb + 5) bytes per cell of max_cells (ntb: third-body reactions).
  * chem_mk_rates: device pointers, asynchronous on `stream`, CHEM_ENOMEM if n > max_cells; not
  * thread-safe (one scratch per object).  chem_mk_destroy synchronizes the device. */

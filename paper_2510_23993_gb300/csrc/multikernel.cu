@@ -149,6 +149,7 @@ int chem_mk_create(const chem_mechanism* m, int64_t max_cells, chem_mk** out) {
   if (!m || m->ns < 1 || m->nr < 1 || m->ns > 127 || !m->W || !m->thermo || !m->nu_f || !m->nu_r || !m->A ||
       !m->b || !m->Ea || !m->reversible || !m->third_body || !m->eff || max_cells < 0 || max_cells > 0x7fffffffLL)
     return CHEM_EINVAL;
+  if (m->nr > 65535) return CHEM_EUNSUPPORTED;   // reactions index the grid's y dimension
   chem_mk* mk = new (std::nothrow) chem_mk();
   if (!mk) return CHEM_ENOMEM;
   if (!open_blas(mk->blas)) {
