@@ -66,3 +66,48 @@ def test_bad_mechanism_rejected_before_device_use(lib, h2mech):
     bad_params = chem.chem_default_params(k_bulk=0)
     m = chem.Mechanism(h2mech)
     assert lib.chem_init(ctypes.byref(m.c), ctypes.byref(bad_params), 10, ctypes.byref(out)) == chem.CHEM_EINVAL
+
+
+def _prototypes():
+    """name -> number of parameters of every chem_* function declared in include/*.h"""
+    out = {}
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if not h.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", h)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"\b(chem_\w+)\s*\(([^;{]*?)\)\s*;", src, flags=re.S):
+            args = m.group(2).strip()
+            out[m.group(1)] = 0 if args in ("", "void") else args.count(",") + 1
+    return out
+
+
+def test_binding_argument_counts_match_the_header(lib):
+    """Every entry point the binding types takes as many arguments as the header declares."""
+    protos = _prototypes()
+    assert len(protos) >= 35
+    checked = 0
+    for name, nargs in protos.items():
+        fn = getattr(lib, name, None)
+        if fn is None or fn.argtypes is None:
+            continue
+        assert len(fn.argtypes) == nargs, (name, len(fn.argtypes), nargs)
+        checked += 1
+    assert checked >= 30
+
+
+def test_new_entry_points_check_arguments_on_the_host(lib):
+    import numpy as np
+    out = ctypes.c_void_p()
+    assert lib.chem_mk_create(None, 10, ctypes.byref(out)) == chem.CHEM_EINVAL
+    nl = ctypes.c_int32(-1)
+    assert lib.chem_advance_explicit(None, None, None, None, 0, None, None, 0, 1e-8, None, 5, 10000,
+                                     ctypes.byref(nl), None) == chem.CHEM_EINVAL
+    assert nl.value == 0
+    W = np.full(9, 0.02)
+    Wp = W.ctypes.data_as(ctypes.c_void_p)
+    assert lib.chem_pressure_layout(9, Wp, 7, None, 0, 0, None, None) == chem.CHEM_EINVAL      # unknown layout
+    assert lib.chem_pressure_layout(9, Wp, chem.CHEM_LAYOUT_SOA, None, 0, 0, None, None) == chem.CHEM_OK   # nothing to do
+    assert lib.chem_pressure_layout(10, np.full(10, 0.02).ctypes.data_as(ctypes.c_void_p), chem.CHEM_LAYOUT_AOS,
+                                    None, 0, 0, None, None) == chem.CHEM_EUNSUPPORTED
+    assert lib.chem_pressure_layout(9, None, chem.CHEM_LAYOUT_AOS, None, 0, 0, None, None) == chem.CHEM_EINVAL
