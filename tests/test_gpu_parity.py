@@ -143,6 +143,14 @@ def test_rates_parity(h2mech):
     ctx.rates(trho, tT, tY, f)
     err = np.abs(f.cpu().numpy() - f_ref) / (scale + 1e-30)
     assert np.max(err) < 3e-5, np.max(err)
+    # the statistic of the paper's App. A: the coefficient of determination of each species'
+    # production rate over the random states (the inert species, identically zero, has none);
+    # errors at the bar above would still give R^2 > 1 - 2e-9
+    fo = f.cpu().numpy().astype(np.float64)
+    for k in range(h2mech["ns"]):
+        ss_tot = np.sum((f_ref[k] - f_ref[k].mean()) ** 2)
+        if ss_tot > 0:
+            assert 1.0 - np.sum((fo[k] - f_ref[k]) ** 2) / ss_tot > 0.999999, k
     ctx.close()
 
 
