@@ -272,9 +272,10 @@ int chem_rates(chem_ctx *ctx, const float *rho, const float *T, const float *Y, 
                int64_t n, float *dYdt, void *stream);
 
 /* chem_advance for callers that cannot allocate device memory (no counterpart in the paper).
- * Callers inside host callbacks or real-time loops, plugins that may only use buffers handed to
- * them, or processes with a capped allocator cannot call chem_init, which allocates.  This entry
- * point takes the mechanism from host memory on every call (same layout as chem_init) and keeps
+ * Real-time loops that may not block on the allocator, plugins that may only use the buffers
+ * handed to them, or processes with a capped allocator cannot call chem_init, which allocates.
+ * This entry point takes the mechanism from host memory on every call (same layout, same checks
+ * and the same packed tables as chem_init, so the results equal chem_advance's) and keeps
  * the packed tables (at most 64 KiB) and its scratch -- the counters and the stiff-cell queue --
  * in fixed-size device arrays that every GPU loading the library holds until the process exits.
  * It calls no cudaMalloc, cudaFree or other allocating routine; the caller passes the device
@@ -286,7 +287,8 @@ int chem_rates(chem_ctx *ctx, const float *rho, const float *T, const float *Y, 
  *   - the host copy of the tables synchronizes `stream` before it starts;
  *   - every call shares the arrays and overwrites them (the counters are cleared first): calls
  *     that overlap on the GPU -- other streams, other threads -- race;
- *   - stats (may be NULL) receives this call's counters; filling it synchronizes `stream`. */
+ *   - stats (may be NULL) receives this call's counters and status; filling it synchronizes
+ *     `stream`.  Without stats a device-side failure shows only in the per-cell counts (-1). */
 int chem_advance_noalloc(const chem_mechanism *mech, const chem_params *params, float *T, float *p,
                          float *Y, int64_t ld, const float *rho, const float *e, int64_t n,
                          double dt, int32_t *substeps, chem_stats *stats, void *stream);

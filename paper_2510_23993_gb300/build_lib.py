@@ -12,11 +12,13 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libchem.so")
-SOURCES = ["abi.cu", "bulk.cu", "stiff.cu", "noalloc.cu", "tune.cu", "mlp.cu", "surrogate.cu", "large.cu", "explicit.cu", "multikernel.cu", "layout.cu"]
+SOURCES = ["abi.cu", "bulk.cu", "stiff.cu", "noalloc.cu", "pack.cu", "tune.cu", "mlp.cu", "surrogate.cu", "large.cu", "explicit.cu", "multikernel.cu", "layout.cu"]
 HEADERS = ["chem_device.cuh", "internal.h", "tc.cuh"]
 NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
+# host code: no contraction of a*b+c into FMA (gcc contracts by default on aarch64 but not on
+# x86-64 without FMA), so the host-packed tables are the same bits on either machine
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2", "-Xcompiler", "-ffp-contract=off",
          "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]
 
 

@@ -3,6 +3,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "../../include/chem.h"
+
 namespace chem {
 
 // Device workspace of one context (counters of the current call; zeroed before each call).
@@ -140,6 +142,19 @@ __host__ __device__ constexpr long long cont_bytes_per_slot(int ns) { return 8LL
 
 constexpr int kBulkBlock = 128;
 constexpr int kStiffBlock = 128;
+
+// species count up to which a mechanism uses the dense table layout (thread per cell); larger
+// mechanisms use the sparse layout and the warp-per-cell kernels of large.cu
+constexpr int kDenseMaxNs = 15;
+
+// host-side checks and table packing (pack.cu), shared by every entry point that takes a mechanism
+int check_mechanism(const chem_mechanism* m);   // CHEM_OK or CHEM_EINVAL
+int check_params(const chem_params* p);         // CHEM_OK or CHEM_EINVAL
+unsigned packed_bytes(const chem_mechanism* m, bool large);
+// Writes the tables of m (dense or large layout) into out[0, packed_bytes) after zeroing it.
+// CHEM_ENOMEM if cap is too small, CHEM_EUNSUPPORTED for a shape the layout cannot hold; *ntb_out
+// (may be null) receives the number of third-body reactions.
+int pack_mechanism(const chem_mechanism* m, bool large, unsigned char* out, size_t cap, int* ntb_out);
 
 // launchers (kernels.cu / stiff.cu); return cudaError_t as int, or -1 for unsupported ns
 int launch_bulk_f32(int ns, const AdvanceArgs<float>& a, int grid, cudaStream_t s);

@@ -111,3 +111,35 @@ def test_new_entry_points_check_arguments_on_the_host(lib):
     assert lib.chem_pressure_layout(10, np.full(10, 0.02).ctypes.data_as(ctypes.c_void_p), chem.CHEM_LAYOUT_AOS,
                                     None, 0, 0, None, None) == chem.CHEM_EUNSUPPORTED
     assert lib.chem_pressure_layout(9, None, chem.CHEM_LAYOUT_AOS, None, 0, 0, None, None) == chem.CHEM_EINVAL
+
+
+@pytest.mark.parametrize("defect", ["A_nonpositive", "nu_4", "eff_negative", "T_range", "W_nan"])
+def test_both_entry_points_refuse_the_same_bad_mechanisms(lib, h2mech, defect):
+    """chem_init and chem_advance_noalloc run the same host-side checks, before any device use,
+    so a mechanism that one refuses the other refuses too (CHEM_EINVAL)."""
+    import numpy as np
+    bad = {k: (np.array(v, copy=True) if isinstance(v, np.ndarray) else v) for k, v in h2mech.items()}
+    if defect == "A_nonpositive":
+        bad["A"][3] = 0.0
+    elif defect == "nu_4":
+        bad["nu_f"][2, 1] = 4
+    elif defect == "eff_negative":
+        r = int(np.nonzero(bad["third_body"])[0][0])
+        bad["eff"][r, 0] = -1.0
+    elif defect == "T_range":
+        bad["thermo"][:, 8] = bad["thermo"][:, 7]   # T_hi == T_lo
+    else:
+        bad["W"][4] = np.nan
+    m = chem.Mechanism(bad)
+    out = ctypes.c_void_p()
+    assert lib.chem_init(ctypes.byref(m.c), None, 10, ctypes.byref(out)) == chem.CHEM_EINVAL
+    assert not out.value
+    rc = lib.chem_advance_noalloc(ctypes.byref(m.c), None, None, None, None, 0, None, None, 0, 1e-8, None, None,
+                                  None)
+    assert rc == chem.CHEM_EINVAL
+    # and the same parameter checks: an unknown flag bit is refused by both
+    good = chem.Mechanism(h2mech)
+    bad_p = chem.chem_default_params(flags=1 << 12)
+    assert lib.chem_init(ctypes.byref(good.c), ctypes.byref(bad_p), 10, ctypes.byref(out)) == chem.CHEM_EINVAL
+    assert lib.chem_advance_noalloc(ctypes.byref(good.c), ctypes.byref(bad_p), None, None, None, 0, None, None, 0,
+                                    1e-8, None, None, None) == chem.CHEM_EINVAL

@@ -279,6 +279,41 @@ def test_single_cell_and_determinism(h2mech):
     ctx.close()
 
 
+def test_result_independent_of_queue_order_and_schedule(h2mech):
+    """Each stiff cell is integrated from its own inputs alone (the cells of Algorithm 3's sparse
+    phase are independent), so the order in which the stiff kernel takes them and the schedule of
+    the stiff phase change nothing: compaction order (no key), the rate-keyed and the
+    previous-count-keyed cost orders, and the two-pass schedule give the same T, p, Y bits, the
+    same per-cell substep counts and the same counters."""
+    T, p, Y, hot = synth.sheet_field(h2mech, n=24, seed=9, frac=0.08)
+    T, p, Y, rho, e = _inputs32(h2mech, T, p, Y)
+    runs = {}
+    prev = None
+    for name, flags in [("compaction", 0), ("order_rate", chem.CHEM_FLAG_ORDER_RATE),
+                        ("order_prev", chem.CHEM_FLAG_ORDER_PREV), ("two_pass", chem.CHEM_FLAG_TWO_PASS),
+                        ("order_rate_two_pass", chem.CHEM_FLAG_ORDER_RATE | chem.CHEM_FLAG_TWO_PASS)]:
+        ctx = chem.Context(h2mech, max_cells=T.size, flags=flags)
+        tT, tp, tY, trho, te = _dev(T, p, Y, rho, e)
+        # ORDER_PREV keys on the counts already in substeps: hand it a previous call's counts
+        sub = torch.from_numpy(prev.copy()).to(DEV) if flags == chem.CHEM_FLAG_ORDER_PREV else \
+            torch.full((T.size,), -99, dtype=torch.int32, device=DEV)
+        rc = chem.chem_advance(ctx.handle, tT, tp, tY, tY.stride(0), trho, te, T.size, 1e-8, sub)
+        st = ctx.status()
+        assert rc == 0 and st["status"] == 0 and st["nqueued"] == int(hot.sum())
+        runs[name] = (tT.cpu().numpy(), tp.cpu().numpy(), tY.cpu().numpy(), sub.cpu().numpy(), st)
+        if prev is None:
+            prev = runs[name][3]
+        ctx.close()
+    ref = runs["compaction"]
+    assert (ref[3] > 1 + 32).sum() > 10   # some cells outlive the two-pass probe
+    for name, r in runs.items():
+        assert np.array_equal(r[0], ref[0]) and np.array_equal(r[1], ref[1]), name
+        assert np.array_equal(r[2], ref[2]), name
+        assert np.array_equal(r[3], ref[3]), name
+        for k in ("nqueued", "nbulk", "substeps", "attempts", "newton", "nfailed"):
+            assert r[4][k] == ref[4][k], (name, k)
+
+
 @pytest.mark.parametrize("order", [0, chem.CHEM_FLAG_ORDER_RATE])
 def test_two_pass_equals_single_pass(h2mech, order):
     """The two-pass stiff phase parks unfinished cells with their full integration state and
