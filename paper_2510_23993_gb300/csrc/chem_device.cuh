@@ -147,38 +147,56 @@ __device__ __forceinline__ int regime_of(float T, float T_lo, float T_hi) {
   return T < T_lo ? 0 : (T > T_hi ? 2 : 1);
 }
 
-// FP64 mixture coefficients E_j = sum_k Y_k c_jk (j = 0..5) and S = sum_k Y_k / W_k.
+// FP64 mixture coefficients E_j = sum_k Y_k c_jk (j = 0..5) and S = sum_k Y_k / W_k.  Outside the
+// fit range (regimes 0 and 2) c_p is frozen, so c_jk = 0 for j >= 2 and only E_0, E_1 are summed.
 template <int NS, typename Y_t>
 __device__ __forceinline__ void mixture64(const MechView& m, int reg, const Y_t* Y, double E[6]) {
   const double* c = m.e64 + reg * NS * 8;
 #pragma unroll
   for (int j = 0; j < 6; ++j) E[j] = 0.0;
+  if (reg == 1) {
 #pragma unroll
-  for (int k = 0; k < NS; ++k) {
-    const double y = static_cast<double>(Y[k]);
+    for (int k = 0; k < NS; ++k) {
+      const double y = static_cast<double>(Y[k]);
 #pragma unroll
-    for (int j = 0; j < 6; ++j) E[j] = fma(y, c[k * 8 + j], E[j]);
+      for (int j = 0; j < 6; ++j) E[j] = fma(y, c[k * 8 + j], E[j]);
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+      const double y = static_cast<double>(Y[k]);
+      E[0] = fma(y, c[k * 8 + 0], E[0]);
+      E[1] = fma(y, c[k * 8 + 1], E[1]);
+    }
   }
 }
 
 // T such that e(T, Y) = e0 (FP64 Newton on the mixture polynomial, bisection safeguard).
+// mix(reg, E) fills E_j = sum_k Y_k c_jk of regime reg (the caller's mixture coefficients).
 // Returns the temperature; *ok is cleared if the root was not found inside [50, 20000] K.
-// *cv_out (optional) receives c_v / R at the solution (J/kg/K divided by R).
-template <int NS, typename Y_t>
-__device__ double temperature_from_energy(const MechView& m, const Y_t* Y, double e0, double T,
-                                          bool* ok, double* cv_out = nullptr) {
+// *cv_out (optional) receives c_v / R at the solution (J/kg/K divided by R).  The iteration stops
+// after a Newton step |dT| <= tol T; the error left is then ~1e-7 |dT| (FP32 reciprocal of c_v)
+// plus the quadratic term (c_v'/2c_v) dT^2 with c_v'/c_v ~ 1e-4 / K: below 1e-14 T for the default
+// tol = 3e-8, below 1e-11 T for tol = 1e-5.
+template <class Mix>
+__device__ __forceinline__ double temperature_newton(const Mix& mix, float T_lo, float T_hi, double e0, double T,
+                                                     bool* ok, double* cv_out, double tol = 3e-8) {
   const double eR = e0 * (1.0 / kR);
   double lo = kTbrLo, hi = kTbrHi;
   if (!(T > lo && T < hi)) T = 1000.0;
-  int reg = regime_of(static_cast<float>(T), m.T_lo, m.T_hi);
-  double E[6];
-  mixture64<NS>(m, reg, Y, E);
+  int reg = regime_of(static_cast<float>(T), T_lo, T_hi);
+  double E[6], D[4];   // D: the coefficients of de/dT, computed once per regime
+  mix(reg, E);
+  D[0] = 2.0 * E[2];
+  D[1] = 3.0 * E[3];
+  D[2] = 4.0 * E[4];
+  D[3] = 5.0 * E[5];
   double cv = 0.0;
   bool conv = false;
 #pragma unroll 1
   for (int it = 0; it < 60; ++it) {
     const double f = fma(T, fma(T, fma(T, fma(T, fma(T, E[5], E[4]), E[3]), E[2]), E[1]), E[0]) - eR;
-    cv = fma(T, fma(T, fma(T, fma(T, 5.0 * E[5], 4.0 * E[4]), 3.0 * E[3]), 2.0 * E[2]), E[1]);
+    cv = fma(T, fma(T, fma(T, fma(T, D[3], D[2]), D[1]), D[0]), E[1]);
     if (f > 0.0) hi = T; else lo = T;
     // Newton step with an FP32 reciprocal of c_v: the step is exact to ~1e-7 relative, so the
     // iteration still converges to the FP64 root (the residual f is FP64).
@@ -186,19 +204,37 @@ __device__ double temperature_from_energy(const MechView& m, const Y_t* Y, doubl
     if (!(Tn > lo && Tn < hi)) Tn = 0.5 * (lo + hi);
     const double dT = Tn - T;
     T = Tn;
-    const int nreg = regime_of(static_cast<float>(T), m.T_lo, m.T_hi);
+    const int nreg = regime_of(static_cast<float>(T), T_lo, T_hi);
     if (nreg != reg) {
       reg = nreg;
-      mixture64<NS>(m, reg, Y, E);
+      mix(reg, E);
+      D[0] = 2.0 * E[2];
+      D[1] = 3.0 * E[3];
+      D[2] = 4.0 * E[4];
+      D[3] = 5.0 * E[5];
       continue;
     }
-    // the step used c_v to ~1e-7 relative, so the error left after it is ~1e-7 |dT| + O(dT^2):
-    // below 1e-14 T once |dT| <= 3e-8 T
-    if (fabs(dT) <= 3e-8 * T) { conv = true; break; }
+    if (fabs(dT) <= tol * T) { conv = true; break; }
   }
   if (cv_out) *cv_out = cv;
   *ok = conv && (T > kTbrLo) && (T < kTbrHi);
   return T;
+}
+
+// The mixture coefficients of the staged tables.
+template <int NS, typename Y_t>
+struct TableMix {
+  const MechView& m;
+  const Y_t* Y;
+  __device__ __forceinline__ void operator()(int reg, double* E) const { mixture64<NS>(m, reg, Y, E); }
+};
+
+// T(e) over the staged tables.
+template <int NS, typename Y_t>
+__device__ double temperature_from_energy(const MechView& m, const Y_t* Y, double e0, double T,
+                                          bool* ok, double* cv_out = nullptr, double tol = 3e-8) {
+  const TableMix<NS, Y_t> mix{m, Y};
+  return temperature_newton(mix, m.T_lo, m.T_hi, e0, T, ok, cv_out, tol);
 }
 
 // ------------------------------------------------------------------ kinetics
