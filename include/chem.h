@@ -293,6 +293,14 @@ int chem_advance_noalloc(const chem_mechanism *mech, const chem_params *params, 
                          float *Y, int64_t ld, const float *rho, const float *e, int64_t n,
                          double dt, int32_t *substeps, chem_stats *stats, void *stream);
 
+/* Measurement utility (no counterpart in the paper): the FP64 FMA throughput of the current GPU in
+ * TFLOP/s (2 flops per FMA), from independent FMA chains filling every SM, best of `reps` timed
+ * launches after one warm-up launch.  The roofline of the stiff integrator, which the FP64 pipe
+ * bounds, is stated against it.  Allocates and frees a small device buffer (stream-ordered) and
+ * synchronizes `stream`.  *tflops (host) receives the result; CHEM_EINVAL for a null pointer or
+ * reps < 1. */
+int chem_measure_fp64_peak(double *tflops, int32_t reps, void *stream);
+
 /* Result of chem_tune. */
 typedef struct {
   int32_t k_bulk;                /* chosen explicit bulk substeps per cell */

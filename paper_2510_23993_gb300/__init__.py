@@ -119,6 +119,8 @@ def lib():
         L.chem_advance_noalloc.argtypes = [_P(chem_mechanism), _P(chem_params), vp, vp, vp, i64, vp, vp, i64, d,
                                            vp, _P(chem_stats), vp]
         L.chem_advance_noalloc.restype = i32
+        L.chem_measure_fp64_peak.argtypes = [_P(ctypes.c_double), i32, vp]
+        L.chem_measure_fp64_peak.restype = i32
         L.chem_boxes_set.argtypes = [vp, _P(chem_box), i32]
         L.chem_advance_boxes.argtypes = [vp, vp]
         L.chem_boxes_capture.argtypes = [vp, vp]
@@ -241,6 +243,13 @@ def chem_advance_explicit(ctx, T, p, Y, ld, rho, e, n, dt, substeps, k_steps=5, 
     rc = lib().chem_advance_explicit(ctx, _dp(T), _dp(p), _dp(Y), int(ld), _dp(rho), _dp(e), int(n), float(dt),
                                      _dp(substeps), int(k_steps), int(n_star), ctypes.byref(nl), _stream(stream))
     return rc, nl.value
+
+
+def chem_measure_fp64_peak(reps=5, stream=None):
+    """FP64 FMA throughput of the current GPU, TFLOP/s (see include/chem.h)."""
+    out = ctypes.c_double(0.0)
+    _check(lib().chem_measure_fp64_peak(ctypes.byref(out), int(reps), _stream(stream)), "chem_measure_fp64_peak")
+    return out.value
 
 
 def chem_advance_noalloc(mech, params, T, p, Y, ld, rho, e, n, dt, substeps, stats=None, stream=None):

@@ -34,8 +34,8 @@ constexpr double kNewtTol = 0.03;   // predicted remaining Newton error below 3%
 // Stopping tolerance of the T(e) inversions (FP64 Newton, Sec. 2.1).  The temperatures of Newton
 // iterates only feed the FP32 rates: a last step |dT| <= 1e-5 T leaves T within ~1e-11 of the root,
 // far below the FP32 resolution of those rates, and saves the confirming iteration of the strict
-// test.  Temperatures of accepted states (written, and the next step's Jacobian) use 3e-8 T (error
-// ~1e-14 T).
+// test.  Temperatures of accepted states (written, and the next step's Jacobian), and every
+// temperature of the FP64-rate mode, use 3e-8 T (error ~1e-14 T).
 constexpr double kTeIterateTol = 1e-5;
 constexpr double kTeStateTol = 3e-8;
 
@@ -216,7 +216,8 @@ __device__ __forceinline__ int newton_iteration(const P& m, const Smem<P::NJ>& s
   constexpr int NS = P::NS;
   ++n_it;
   bool ok;
-  Tz = m.temperature(z, c.e0, Tz, &ok, nullptr, kTeIterateTol);
+  // FP64 rates (CHEM_FLAG_FP64_RATES) resolve T beyond FP32: their iterates keep the strict tolerance
+  Tz = m.temperature(z, c.e0, Tz, &ok, nullptr, c.fp64_rates ? kTeStateTol : kTeIterateTol);
   if (!ok) return -1;
   float F[NS], Zf[NS];
 #pragma unroll

@@ -71,12 +71,13 @@ def sheet_field(mech, n=128, frac=0.05, seed=0, alpha=0.5, nx=None, ny=None, nz=
     return T, p, Y, hot
 
 
-def stratified_sample(hot, n_sample, seed=0):
-    """Seeded subsample of cell indices keeping the hot fraction of the full field."""
+def stratified_sample(hot, n_sample, seed=0, hot_frac=None):
+    """Seeded subsample of cell indices keeping the hot fraction of the full field (or hot_frac)."""
     rng = np.random.default_rng(seed + 7919)
     hot_idx = np.nonzero(hot)[0]
     cold_idx = np.nonzero(~hot)[0]
-    n_hot = int(round(n_sample * len(hot_idx) / max(1, len(hot))))
+    frac = len(hot_idx) / max(1, len(hot)) if hot_frac is None else hot_frac
+    n_hot = int(round(n_sample * frac))
     n_hot = min(n_hot, len(hot_idx))
     n_cold = min(n_sample - n_hot, len(cold_idx))
     pick = np.concatenate([rng.choice(hot_idx, n_hot, replace=False),

@@ -143,3 +143,10 @@ def test_both_entry_points_refuse_the_same_bad_mechanisms(lib, h2mech, defect):
     assert lib.chem_init(ctypes.byref(good.c), ctypes.byref(bad_p), 10, ctypes.byref(out)) == chem.CHEM_EINVAL
     assert lib.chem_advance_noalloc(ctypes.byref(good.c), ctypes.byref(bad_p), None, None, None, 0, None, None, 0,
                                     1e-8, None, None, None) == chem.CHEM_EINVAL
+
+
+def test_fp64_peak_measurement_checks_arguments_on_the_host(lib):
+    out = ctypes.c_double(-1.0)
+    assert lib.chem_measure_fp64_peak(None, 5, None) == chem.CHEM_EINVAL
+    assert lib.chem_measure_fp64_peak(ctypes.byref(out), 0, None) == chem.CHEM_EINVAL
+    assert out.value == -1.0   # nothing written on a refused call

@@ -395,3 +395,14 @@ def test_full_size_sheet_sampled(h2mech):
     cond = _conditioning(h2mech, rho[idx], e[idx], T[idx], Y[:, idx], 1e-8, T_ref, Y_ref)
     print("full-size sampled parity", _parity(To[idx], Yo[:, idx], T_ref, Y_ref, cond=cond))
     ctx.close()
+
+
+def test_fp64_peak_measurement_is_plausible():
+    """The FMA-chain measurement that the stiff kernel's roofline is stated against: positive, and
+    within a factor of two of the unit-count figure of this part (152 SMs x 2 FP64 FMA per clock at
+    up to 2.07 GHz, 1.26 TFLOP/s); repeated measurements agree to 15%."""
+    a = chem.chem_measure_fp64_peak(reps=3)
+    b = chem.chem_measure_fp64_peak(reps=3)
+    unit = 152 * 2 * 2 * 2.07e9 / 1e12
+    assert 0.5 * unit < a < 2.0 * unit
+    assert abs(a - b) <= 0.15 * max(a, b)
