@@ -339,7 +339,7 @@ int chem_tc_gemm(const float *A, int64_t sam, int64_t sak, const float *B, int64
 /* ---------------------------------------------------------------------------------------------
  * Learned surrogate of the chemistry step with a per-cell error gate.  The paper has no
  * counterpart (its outlook, Sec. 6, mentions machine learning only for performance prediction).  The network
- * (compiled for ns = 9) maps x = (T, ln p, ln dt, ln(Y_k + 1e-6)), standardised, through four
+ * (compiled for ns = 9 and ns = 53) maps x = (T, ln p, ln dt, ln(Y_k + 1e-6)), standardised, through four
  * GELU layers of 128 to ns + 2 outputs: the standardised encodings a = asinh(u / 1e-8) of
  * u_k = ln((Y1_k + 1e-6) / (max(Y_k, 0) + 1e-6)) and u_T = ln(T1 / T) for the state (Y1, T1)
  * after dt (decoded with u clamped so that 0 <= Y1 <= 1 and T / 10 <= T1 <= 10 T), and an error head
@@ -361,19 +361,25 @@ typedef struct {
 /* Create (or re-initialise) the context's surrogate: He-initialised weights from `seed`, zero
  * AdamW moments, an empty training box (nothing is accepted until it is trained or loaded) and
  * the conserved directions of the mechanism (the complement of the span of the reaction vectors
- * W .* (nu_r - nu_f)).  CHEM_EUNSUPPORTED if ns != 9 or more than 4 directions are conserved. */
+ * W .* (nu_r - nu_f)).  CHEM_EUNSUPPORTED if ns is not 9 or 53, or more than 8 directions are
+ * conserved. */
 int chem_surrogate_init(chem_ctx *ctx, uint64_t seed);
 
-/* Number of FP32 parameters (weights and biases of the five layers, W_l row-major [out][in]
- * followed by b_l, layer by layer). */
-int chem_surrogate_nparams(void);
+/* Number of FP32 parameters of the network for a mechanism of ns species (weights and biases of
+ * the five layers, W_l row-major [out][in] followed by b_l, layer by layer): 52,619 for ns = 9,
+ * 63,927 for ns = 53; CHEM_EUNSUPPORTED for other species counts. */
+int chem_surrogate_nparams(int32_t ns);
 
-/* Train on n samples (device arrays): X [n][12] rows (T [K], p [Pa], dt [s], Y_1..Y_9) and
- * Yt [n][10] rows (Y1_1..Y1_9, T1), the state after dt (a standard deviation below 1e-12 is
- * replaced by 1).  Sets the normalisation
- * and the training box (range of every feature) from the data, then runs cfg->epochs epochs of shuffled full batches
- * (forward and backward on the tensor cores, AdamW).  loss_per_epoch (host, [epochs], or null)
- * receives the mean batch loss of each epoch.  Synchronous; returns CHEM_ECUDA if a
+/* Train on n samples (device arrays): X [n][ns + 3] rows (T [K], p [Pa], dt [s], Y_1..Y_ns) and
+ * Yt [n][ns + 1] rows (Y1_1..Y1_ns, T1), the state after dt.  Sets the normalisation (mean and
+ * standard deviation of every feature and target encoding; a standard deviation below 1e-12 is
+ * replaced by 1) and the training box (range of every feature) from the data, then runs
+ * cfg->epochs epochs of shuffled full batches: forward and backward on the tensor cores, then one
+ * AdamW update per batch, m = 0.9 m + 0.1 g, v = 0.999 v + 0.001 g^2,
+ * w -= lr_s (m / (1 - 0.9^t) / (sqrt(v / (1 - 0.999^t)) + 1e-8) + weight_decay w), with t the
+ * optimiser step count since chem_surrogate_init and lr_s = cfg->lr (1 + cos(pi s / S)) / 2 for
+ * step s = 0 .. S - 1 of this call (S = epochs x n / batch).  loss_per_epoch (host, [epochs], or
+ * null) receives the mean batch loss of each epoch.  Synchronous; returns CHEM_ECUDA if a
  * tensor-core wait timed out. */
 int chem_surrogate_train(chem_ctx *ctx, const float *X, const float *Yt, int64_t n, const chem_train_cfg *cfg,
                          float *loss_per_epoch, void *stream);
@@ -387,12 +393,12 @@ int chem_surrogate_train(chem_ctx *ctx, const float *X, const float *Yt, int64_t
 int chem_surrogate_grads(chem_ctx *ctx, const float *X, const float *Yt, int32_t n, float err_weight,
                          float *grads, float *loss, void *stream);
 
-/* Network outputs (standardised, [n][11], device) of the GEMM path for X [n][12] (device). */
+/* Network outputs (standardised, [n][ns + 2], device) of the GEMM path for X [n][ns + 3] (device). */
 int chem_surrogate_forward(chem_ctx *ctx, const float *X, int32_t n, float *out, void *stream);
 
 /* Network outputs of the fused inference kernel of chem_advance_gated for n cells in the SoA
- * layout of chem_advance (T, Y [9][ld], rho, e on the device; p is derived), [n][11] into out.
- * The state is not modified.  Synchronous. */
+ * layout of chem_advance (T, Y [ns][ld], rho, e on the device; p is derived), [n][ns + 2] into
+ * out.  The state is not modified.  Synchronous. */
 int chem_surrogate_infer(chem_ctx *ctx, const float *T, const float *Y, int64_t ld, const float *rho,
                          const float *e, int64_t n, double dt, float *out, void *stream);
 

@@ -19,7 +19,15 @@ documents it, written out plainly in numpy FP64:
   the directions no reaction moves Y in;
 * the training loss mean_b [ sum_j (o_bj - t_bj)^2 + w (o_b,err - e*_b)^2 ] with
   e*_b = log10(E_b + 1e-12) held constant, E_b the relative error of the corrected state;
-* its gradient by plain reverse-mode differentiation (chain rule, layer by layer).
+* its gradient by plain reverse-mode differentiation (chain rule, layer by layer);
+* the optimiser: AdamW, i.e. Adam's bias-corrected first and second moment estimates (Kingma &
+  Ba, "Adam: a method for stochastic optimization", 2015) with the weight decay decoupled from
+  the adaptive step (Loshchilov & Hutter, "Decoupled weight decay regularization", 2019), scaled
+  by a cosine-annealed learning rate lr_s = lr (1 + cos(pi s / S)) / 2 (their SGDR schedule,
+  one cycle without restart).
+
+Everything is written for any species count ns: the network maps ns + 3 features to ns + 2
+outputs (ns + 1 targets and the error head).
 
 `bf16_products=True` rounds both operands of every matrix product to bfloat16 (round to nearest even)
 before multiplying, as the interface states the tensor-core path does; everything else stays
@@ -35,22 +43,31 @@ import numpy as np
 
 EPS_Y = 1e-6     # Y floor of the log features and of the relative error
 U0 = 1e-8        # linear range of the asinh compression
-NS = 9
-N_IN = NS + 3
-N_OUT = NS + 2
-N_TGT = NS + 1
 HIDDEN = 128
-MAX_CONS = 4
-WIDTHS = (N_IN, HIDDEN, HIDDEN, HIDDEN, HIDDEN, N_OUT)
+MAX_CONS = 8
+
+
+def widths(ns):
+    """Layer widths of the network for ns species: ns + 3 inputs, four hidden layers, ns + 2 outputs."""
+    return (ns + 3, HIDDEN, HIDDEN, HIDDEN, HIDDEN, ns + 2)
 
 
 # ------------------------------------------------------------------ parameters
 
-def n_params(widths=WIDTHS):
-    return sum(widths[l + 1] * widths[l] + widths[l + 1] for l in range(len(widths) - 1))
+def n_params(ns):
+    w = widths(ns)
+    return sum(w[l + 1] * w[l] + w[l + 1] for l in range(len(w) - 1))
 
 
-def unflatten(flat, widths=WIDTHS):
+def ns_of_params(n):
+    """Species count of a flat parameter vector of n entries."""
+    for ns in range(1, 1024):
+        if n_params(ns) == n:
+            return ns
+    raise ValueError(f"no network has {n} parameters")
+
+
+def unflatten(flat, widths):
     """Flat parameter vector (W_1 row-major [out][in], b_1, W_2, b_2, ...) -> [(W, b), ...]."""
     flat = np.asarray(flat, dtype=np.float64)
     layers, off = [], 0
@@ -71,27 +88,30 @@ def flatten(layers):
 
 # ------------------------------------------------------------------ normalisation block
 
-NORM_FIELDS = (("mu_x", N_IN), ("sd_x", N_IN), ("mu_y", N_TGT), ("sd_y", N_TGT), ("lo_x", N_IN), ("hi_x", N_IN),
-               ("C", MAX_CONS * NS))
+def norm_fields(ns):
+    return (("mu_x", ns + 3), ("sd_x", ns + 3), ("mu_y", ns + 1), ("sd_y", ns + 1), ("lo_x", ns + 3), ("hi_x", ns + 3),
+            ("C", MAX_CONS * ns))
 
 
 def pack_checkpoint(norm, params):
     """Bytes of a surrogate checkpoint: int32 header ("CHSG", version 1, ns, nparams), the
     normalisation block (float32 fields, then int32 ncons and 3 pad words) and float32 params."""
-    hdr = np.array([0x47534843, 1, NS, n_params()], dtype=np.int32).tobytes()
-    body = b"".join(np.asarray(norm[k], dtype=np.float32).reshape(n).tobytes() for k, n in NORM_FIELDS)
+    ns = len(norm["mu_y"]) - 1
+    hdr = np.array([0x47534843, 1, ns, n_params(ns)], dtype=np.int32).tobytes()
+    body = b"".join(np.asarray(norm[k], dtype=np.float32).reshape(n).tobytes() for k, n in norm_fields(ns))
     tail = np.array([norm["ncons"], 0, 0, 0], dtype=np.int32).tobytes()
     return hdr + body + tail + np.asarray(params, dtype=np.float32).tobytes()
 
 
 def unpack_checkpoint(blob):
     hdr = np.frombuffer(blob[:16], dtype=np.int32)
-    assert hdr[0] == 0x47534843 and hdr[1] == 1 and hdr[2] == NS
+    assert hdr[0] == 0x47534843 and hdr[1] == 1
+    ns = int(hdr[2])
     off, norm = 16, {}
-    for k, n in NORM_FIELDS:
+    for k, n in norm_fields(ns):
         norm[k] = np.frombuffer(blob[off:off + 4 * n], dtype=np.float32).astype(np.float64)
         off += 4 * n
-    norm["C"] = norm["C"].reshape(MAX_CONS, NS)
+    norm["C"] = norm["C"].reshape(MAX_CONS, ns)
     norm["ncons"] = int(np.frombuffer(blob[off:off + 4], dtype=np.int32)[0])
     off += 16
     params = np.frombuffer(blob[off:], dtype=np.float32).astype(np.float64)
@@ -108,10 +128,19 @@ def conserved_basis(elem, W):
     return q[:, keep].T
 
 
+def conserved_directions(W, nu_f, nu_r):
+    """Orthonormal rows spanning the complement of span{W .* (nu_r - nu_f)_r}: every direction of
+    Y that no reaction moves (the element masses, and a species that no reaction touches).  The
+    null space of the reaction matrix by singular value decomposition."""
+    from scipy.linalg import null_space
+    R = (np.asarray(W, float)[:, None] * (np.asarray(nu_r, float) - np.asarray(nu_f, float)).T)   # [ns][nr]
+    return null_space(R.T).T
+
+
 # ------------------------------------------------------------------ encodings
 
 def features(T, p, dt, Y):
-    """[n][12] raw features; Y is [n][ns]."""
+    """[n][ns + 3] raw features; Y is [n][ns]."""
     T, p, dt = (np.asarray(v, float).reshape(-1) for v in (T, p, dt))
     Y = np.asarray(Y, float)
     return np.column_stack([T, np.log(p), np.log(dt), np.log(np.maximum(Y, 0.0) + EPS_Y)])
@@ -139,7 +168,7 @@ def decode_temperature(a, T0):
 
 
 def targets(T0, Y0, Y1, T1):
-    """[n][10] raw target encodings of the state (Y1, T1) after dt."""
+    """[n][ns + 1] raw target encodings of the state (Y1, T1) after dt."""
     base = np.maximum(np.asarray(Y0, float), 0.0) + EPS_Y
     aY = encode(np.log((np.asarray(Y1, float) + EPS_Y) / base))
     aT = encode(np.log(np.asarray(T1, float).reshape(-1) / np.asarray(T0, float).reshape(-1)))
@@ -162,10 +191,11 @@ def conserve(C, Y0, dY):
 
 
 def decode_state(norm, o, Y0, T0):
-    """Standardised outputs o [n][>=10] -> conservative new state Y1 [n][ns] and T1 [n]."""
-    a = o[:, :N_TGT] * norm["sd_y"] + norm["mu_y"]
-    Y1 = decode_species(a[:, :NS], Y0)
-    T1 = decode_temperature(a[:, NS], T0)
+    """Standardised outputs o [n][>= ns + 1] -> conservative new state Y1 [n][ns] and T1 [n]."""
+    ns = Y0.shape[1]
+    a = o[:, :ns + 1] * norm["sd_y"] + norm["mu_y"]
+    Y1 = decode_species(a[:, :ns], Y0)
+    T1 = decode_temperature(a[:, ns], T0)
     C = norm["C"][:norm["ncons"]]
     return Y0 + conserve(C, Y0, Y1 - Y0), T1
 
@@ -228,15 +258,16 @@ def forward(layers, x, bf16_products=False):
 
 def loss_and_grad(layers, x, t, e_star, err_weight, bf16_products=False):
     """Loss of a batch and its gradient (list of (dW, db)) by reverse-mode differentiation.
-    x [B][n_in] standardised inputs, t [B][10] standardised targets, e_star [B]."""
+    x [B][n_in] standardised inputs, t [B][ns + 1] standardised targets, e_star [B]."""
     B = x.shape[0]
+    nt = t.shape[1]
     o, (zs, acts) = forward(layers, x, bf16_products)
-    r = o[:, :N_TGT] - t
-    de = o[:, N_TGT] - e_star
+    r = o[:, :nt] - t
+    de = o[:, nt] - e_star
     loss = (np.sum(r * r) + err_weight * np.sum(de * de)) / B
     dz = np.zeros_like(o)
-    dz[:, :N_TGT] = 2.0 * r / B
-    dz[:, N_TGT] = 2.0 * err_weight * de / B
+    dz[:, :nt] = 2.0 * r / B
+    dz[:, nt] = 2.0 * err_weight * de / B
     grads = [None] * len(layers)
     for l in range(len(layers) - 1, -1, -1):
         W, _ = layers[l]
@@ -254,12 +285,13 @@ def loss_and_grad(layers, x, t, e_star, err_weight, bf16_products=False):
 
 def surrogate_loss_and_grad(norm, params, Xraw, Yraw, err_weight, bf16_products=False):
     """The documented training loss of one batch in the library's data layout: Xraw rows
-    (T, p, dt, Y[9]), Yraw rows (Y1[9], T1), the state after dt.  Returns (loss, flat gradient)."""
+    (T, p, dt, Y[ns]), Yraw rows (Y1[ns], T1), the state after dt.  Returns (loss, flat gradient)."""
+    ns = Xraw.shape[1] - 3
     T0, p, dt, Y0 = Xraw[:, 0], Xraw[:, 1], Xraw[:, 2], Xraw[:, 3:]
-    Y1, T1 = Yraw[:, :NS], Yraw[:, NS]
+    Y1, T1 = Yraw[:, :ns], Yraw[:, ns]
     x = standardise_inputs(norm, features(T0, p, dt, Y0))
     t = (targets(T0, Y0, Y1, T1) - norm["mu_y"]) / norm["sd_y"]
-    layers = unflatten(params)
+    layers = unflatten(params, widths(ns))
     o, _ = forward(layers, x, bf16_products)
     e_star = np.log10(state_error(norm, o, Y0, T0, Y1, T1) + 1e-12)
     loss, grads = loss_and_grad(layers, x, t, e_star, err_weight, bf16_products)
@@ -267,7 +299,27 @@ def surrogate_loss_and_grad(norm, params, Xraw, Yraw, err_weight, bf16_products=
 
 
 def surrogate_outputs(norm, params, Xraw, bf16_products=False):
-    """Standardised network outputs [n][11] for raw rows (T, p, dt, Y[9])."""
+    """Standardised network outputs [n][ns + 2] for raw rows (T, p, dt, Y[ns])."""
     x = standardise_inputs(norm, features(Xraw[:, 0], Xraw[:, 1], Xraw[:, 2], Xraw[:, 3:]))
-    o, _ = forward(unflatten(params), x, bf16_products)
+    o, _ = forward(unflatten(params, widths(Xraw.shape[1] - 3)), x, bf16_products)
     return o
+
+
+# ------------------------------------------------------------------ optimiser
+
+def cosine_lr(lr, step, total):
+    """Learning rate of step s = 0 .. total - 1: lr (1 + cos(pi s / total)) / 2."""
+    return 0.5 * lr * (1.0 + math.cos(math.pi * step / total))
+
+
+def adamw_step(w, g, m, v, t, lr, weight_decay, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One AdamW update of parameters w with gradient g at optimiser step t (1-based) and learning
+    rate lr; returns the new (w, m, v).  m and v are Adam's running first and second moment
+    estimates, divided by 1 - beta^t for the bias of their zero start; the decay of the weights is
+    decoupled from the adaptive step and scaled by the same learning rate."""
+    m = beta1 * m + (1.0 - beta1) * g
+    v = beta2 * v + (1.0 - beta2) * g * g
+    m_hat = m / (1.0 - beta1 ** t)
+    v_hat = v / (1.0 - beta2 ** t)
+    w = w - lr * (m_hat / (np.sqrt(v_hat) + eps) + weight_decay * w)
+    return w, m, v

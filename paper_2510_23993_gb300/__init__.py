@@ -133,7 +133,7 @@ def lib():
         L.chem_tc_gemm.restype = i32
         u64, szt = ctypes.c_uint64, ctypes.c_size_t
         L.chem_surrogate_init.argtypes = [vp, u64]
-        L.chem_surrogate_nparams.argtypes = []
+        L.chem_surrogate_nparams.argtypes = [i32]
         L.chem_surrogate_train.argtypes = [vp, vp, vp, i64, _P(chem_train_cfg), vp, vp]
         L.chem_surrogate_grads.argtypes = [vp, vp, vp, i32, ctypes.c_float, vp, vp, vp]
         L.chem_surrogate_forward.argtypes = [vp, vp, i32, vp, vp]
@@ -269,12 +269,12 @@ def chem_surrogate_init(ctx, seed=0):
     return lib().chem_surrogate_init(ctx, int(seed))
 
 
-def chem_surrogate_nparams():
-    return lib().chem_surrogate_nparams()
+def chem_surrogate_nparams(ns):
+    return lib().chem_surrogate_nparams(int(ns))
 
 
 def chem_surrogate_train(ctx, X, Yt, n, cfg, loss_per_epoch=None, stream=None):
-    """X [n][12] = (T, p, dt, Y[9]), Yt [n][10] = (dY[9], dT), device; loss_per_epoch: ctypes float array."""
+    """X [n][ns + 3] = (T, p, dt, Y), Yt [n][ns + 1] = (Y1, T1), device; loss_per_epoch: ctypes float array."""
     return lib().chem_surrogate_train(ctx, _dp(X), _dp(Yt), int(n), ctypes.byref(cfg), loss_per_epoch,
                                       _stream(stream))
 
@@ -497,8 +497,8 @@ class Context:
 
     def surrogate_train(self, X, Yt, epochs=20, batch=4096, lr=1e-3, weight_decay=1e-5, err_weight=0.1, seed=0,
                         stream=None):
-        """Train on device arrays X [n][12] = (T, p, dt, Y[9]) and Yt [n][10] = (dY[9], dT); returns the
-        mean loss of each epoch."""
+        """Train on device arrays X [n][ns + 3] = (T, p, dt, Y) and Yt [n][ns + 1] = (Y1, T1), the state
+        after dt; returns the mean loss of each epoch."""
         for t in (X, Yt):
             if not t.is_cuda or not t.is_contiguous() or t.dtype.itemsize != 4:
                 raise ValueError("X and Yt must be contiguous float32 CUDA tensors")

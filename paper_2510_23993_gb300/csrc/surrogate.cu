@@ -9,7 +9,8 @@
 // relative error of the new Y_k + eps: the accuracy the 1e-4 parity bar asks for on Y_k >= 1e-6
 // (and 1e-10 absolute below) is reached on every cell whose change is small enough, whatever
 // its size class.  Weights are FP32 masters, rounded to BF16 for every tensor-core product
-// (FP32 accumulation in TMEM).
+// (FP32 accumulation in TMEM).  The code is a template over the species count; the library
+// compiles it for the 9-species (12 -> 11) and the 53-species (56 -> 55) mechanisms.
 //
 // Training (chem_surrogate_train): mini-batch AdamW with cosine learning-rate decay; forward and
 // backward are tensor-core GEMMs of mlp.cu (forward X W^T, backward-data dZ W, backward-weight
@@ -59,45 +60,57 @@ int launch_gemm(const GemmArgs& g, int ksplit, cudaStream_t s);
 namespace sg {
 
 constexpr int kH = 128;        // hidden width
-constexpr int kNS = 9;         // species of the compiled surrogate
-constexpr int kNIn = kNS + 3;  // inputs
-constexpr int kNOut = kNS + 2; // outputs: a(dY), a(dT), log10 error
-constexpr int kNTgt = kNS + 1; // regression targets
-constexpr int kKIn = 16;       // input K padded for the tensor core
-constexpr int kNOutPad = 16;   // output N padded
-constexpr int kRaw = 2 * kNS + 2;   // raw per-sample record of a batch: Y0[ns], T0, Y1[ns], T1
-constexpr int kMaxCons = 4;    // conserved directions (elements) supported
+constexpr int kMaxCons = 8;    // conserved directions supported (elements, plus species no reaction touches)
 constexpr float kEps = 1e-6f;  // Y floor of the log features and of the relative error
 constexpr float kU0 = 1e-8f;   // linear range of the asinh compression of u
 
-// flat parameter offsets (FP32 masters); W_l is [out][in] row-major
-constexpr int oW1 = 0, oB1 = oW1 + kH * kNIn;
-constexpr int oW2 = oB1 + kH, oB2 = oW2 + kH * kH;
-constexpr int oW3 = oB2 + kH, oB3 = oW3 + kH * kH;
-constexpr int oW4 = oB3 + kH, oB4 = oW4 + kH * kH;
-constexpr int oW5 = oB4 + kH, oB5 = oW5 + kNOut * kH;
-constexpr int kNParams = oB5 + kNOut;
+// Shapes of the network for NS species.
+template <int NS>
+struct Dims {
+  static constexpr int kNIn = NS + 3;                      // inputs
+  static constexpr int kNOut = NS + 2;                     // outputs: a(dY), a(dT), log10 error
+  static constexpr int kNTgt = NS + 1;                     // regression targets
+  static constexpr int kKIn = (kNIn + 15) / 16 * 16;       // input K padded for the tensor core
+  static constexpr int kNOutPad = (kNOut + 15) / 16 * 16;  // output N padded
+  static constexpr int kRaw = 2 * NS + 2;                  // raw batch record: Y0[ns], T0, Y1[ns], T1
+  // flat parameter offsets (FP32 masters); W_l is [out][in] row-major
+  static constexpr int oW1 = 0, oB1 = oW1 + kH * kNIn;
+  static constexpr int oW2 = oB1 + kH, oB2 = oW2 + kH * kH;
+  static constexpr int oW3 = oB2 + kH, oB3 = oW3 + kH * kH;
+  static constexpr int oW4 = oB3 + kH, oB4 = oW4 + kH * kH;
+  static constexpr int oW5 = oB4 + kH, oB5 = oW5 + kNOut * kH;
+  static constexpr int kNParams = oB5 + kNOut;
+  // packed inference blob (shared-memory image): BF16 weights in the K-major core-matrix layout
+  // followed by FP32 biases and the Norm block
+  static constexpr int bW1 = 0;                          // 128 x kKIn
+  static constexpr int bW2 = bW1 + kH * kKIn * 2;        // 128 x 128
+  static constexpr int bW3 = bW2 + kH * kH * 2;
+  static constexpr int bW4 = bW3 + kH * kH * 2;
+  static constexpr int bW5 = bW4 + kH * kH * 2;          // kNOutPad x 128
+  static constexpr int bBias = bW5 + kNOutPad * kH * 2;  // b1..b4 [4][128], b5 [kNOutPad]
+  static constexpr int bNorm = bBias + (4 * kH + kNOutPad) * 4;
+  // layer shapes (inputs, outputs) and parameter offsets
+  static constexpr int in(int l) { return l == 0 ? kNIn : kH; }
+  static constexpr int out(int l) { return l == 4 ? kNOut : kH; }
+  static constexpr int wo(int l) { return l == 0 ? oW1 : l == 1 ? oW2 : l == 2 ? oW3 : l == 3 ? oW4 : oW5; }
+  static constexpr int bo(int l) { return l == 0 ? oB1 : l == 1 ? oB2 : l == 2 ? oB3 : l == 3 ? oB4 : oB5; }
+};
 
 // normalisation, training box and conservation constraints (FP32)
+template <int NS>
 struct Norm {
-  float mu_x[kNIn], sd_x[kNIn];
-  float mu_y[kNTgt], sd_y[kNTgt];
-  float lo_x[kNIn], hi_x[kNIn];    // training box of the (unstandardised) features
-  float C[kMaxCons][kNS];          // orthonormal basis of the directions no reaction moves Y in
+  float mu_x[NS + 3], sd_x[NS + 3];
+  float mu_y[NS + 1], sd_y[NS + 1];
+  float lo_x[NS + 3], hi_x[NS + 3];    // training box of the (unstandardised) features
+  float C[kMaxCons][NS];               // orthonormal basis of the directions no reaction moves Y in
   int ncons;
   int pad[3];
 };
 
-// packed inference blob (shared-memory image): BF16 weights in the K-major core-matrix layout
-// followed by FP32 biases and the Norm block
-constexpr int bW1 = 0;                          // 128 x 16
-constexpr int bW2 = bW1 + kH * kKIn * 2;        // 128 x 128
-constexpr int bW3 = bW2 + kH * kH * 2;
-constexpr int bW4 = bW3 + kH * kH * 2;
-constexpr int bW5 = bW4 + kH * kH * 2;          // 16 x 128
-constexpr int bBias = bW5 + kNOutPad * kH * 2;  // b1..b4 [4][128], b5 [16]
-constexpr int bNorm = bBias + (4 * kH + kNOutPad) * 4;
-constexpr int kBlobBytes = ((bNorm + static_cast<int>(sizeof(Norm))) + 15) & ~15;
+template <int NS>
+constexpr int blob_bytes() {
+  return ((Dims<NS>::bNorm + static_cast<int>(sizeof(Norm<NS>))) + 15) & ~15;
+}
 
 __device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
 __device__ __forceinline__ float gelu_grad(float x) {
@@ -106,12 +119,13 @@ __device__ __forceinline__ float gelu_grad(float x) {
 
 // ------------------------------------------------------------------ encoding (shared by training and inference)
 
+template <int NS>
 __device__ __forceinline__ void features(float T, float p, float lndt, const float* y, float* x) {
   x[0] = T;
   x[1] = logf(p);
   x[2] = lndt;
 #pragma unroll
-  for (int k = 0; k < kNS; ++k) x[3 + k] = logf(fmaxf(y[k], 0.0f) + kEps);
+  for (int k = 0; k < NS; ++k) x[3 + k] = logf(fmaxf(y[k], 0.0f) + kEps);
 }
 
 // u = ln((x1 + c) / (x0 + c)) without cancellation: log1p of the (exact, nearby) difference when
@@ -137,19 +151,20 @@ constexpr float kLnTen = 2.302585092994046f;
 // conservative correction of the new mass fractions y1 (change dY = y1 - y0): the smallest
 // change in the norm sum_k (delta_k / w_k)^2, w_k = max(|y1_k|, eps), that makes C dY = 0.  With
 // B = C diag(w) and B^T = Q R (modified Gram-Schmidt, FP64), delta = -diag(w) Q R^{-T} (C dY).
-__device__ __forceinline__ void conserve(const Norm& nm, const float* y0, float* y1) {
+template <int NS>
+__device__ __forceinline__ void conserve(const Norm<NS>& nm, const float* y0, float* y1) {
   const int m = nm.ncons;
   if (m <= 0) return;
-  double w[kNS], q[kMaxCons][kNS], R[kMaxCons][kMaxCons], y[kMaxCons];
+  double w[NS], q[kMaxCons][NS], R[kMaxCons][kMaxCons], y[kMaxCons];
 #pragma unroll
-  for (int k = 0; k < kNS; ++k) w[k] = fmax(fabs(static_cast<double>(y1[k])), static_cast<double>(kEps));
+  for (int k = 0; k < NS; ++k) w[k] = fmax(fabs(static_cast<double>(y1[k])), static_cast<double>(kEps));
 #pragma unroll
   for (int i = 0; i < kMaxCons; ++i) {
     y[i] = 0.0;
     if (i >= m) continue;
     double r = 0.0;
 #pragma unroll
-    for (int k = 0; k < kNS; ++k) {
+    for (int k = 0; k < NS; ++k) {
       q[i][k] = w[k] * nm.C[i][k];
       r += nm.C[i][k] * (static_cast<double>(y1[k]) - static_cast<double>(y0[k]));
     }
@@ -157,26 +172,26 @@ __device__ __forceinline__ void conserve(const Norm& nm, const float* y0, float*
     for (int j = 0; j < i; ++j) {
       double d = 0.0;
 #pragma unroll
-      for (int k = 0; k < kNS; ++k) d += q[j][k] * q[i][k];
+      for (int k = 0; k < NS; ++k) d += q[j][k] * q[i][k];
       R[j][i] = d;
 #pragma unroll
-      for (int k = 0; k < kNS; ++k) q[i][k] -= d * q[j][k];
+      for (int k = 0; k < NS; ++k) q[i][k] -= d * q[j][k];
     }
     double nrm = 0.0;
 #pragma unroll
-    for (int k = 0; k < kNS; ++k) nrm += q[i][k] * q[i][k];
+    for (int k = 0; k < NS; ++k) nrm += q[i][k] * q[i][k];
     nrm = sqrt(nrm);
     R[i][i] = nrm;
     const double inv = nrm > 1e-300 ? 1.0 / nrm : 0.0;
 #pragma unroll
-    for (int k = 0; k < kNS; ++k) q[i][k] *= inv;
+    for (int k = 0; k < NS; ++k) q[i][k] *= inv;
     // forward substitution of R^T y = C dY (a degenerate direction contributes nothing)
 #pragma unroll
     for (int j = 0; j < i; ++j) r -= R[j][i] * y[j];
     y[i] = r * inv;
   }
 #pragma unroll
-  for (int k = 0; k < kNS; ++k) {
+  for (int k = 0; k < NS; ++k) {
     double z = 0.0;
 #pragma unroll
     for (int i = 0; i < kMaxCons; ++i)
@@ -186,89 +201,96 @@ __device__ __forceinline__ void conserve(const Norm& nm, const float* y0, float*
 }
 
 // network outputs o (standardised) -> conservative new mass fractions y1 and temperature T1
-__device__ __forceinline__ void decode_state(const Norm& nm, const float* o, const float* y0, float T0, float* y1,
+template <int NS>
+__device__ __forceinline__ void decode_state(const Norm<NS>& nm, const float* o, const float* y0, float T0, float* y1,
                                              float* T1) {
 #pragma unroll
-  for (int k = 0; k < kNS; ++k) {
+  for (int k = 0; k < NS; ++k) {
     const float y0c = fmaxf(y0[k], 0.0f);
     const float lb = logf(y0c + kEps);
     const float u = decode_u(o[k] * nm.sd_y[k] + nm.mu_y[k], kLnEps - lb, log1pf(kEps) - lb);
     y1[k] = apply_u(y0c, kEps, u);
   }
-  *T1 = apply_u(T0, 0.0f, decode_u(o[kNS] * nm.sd_y[kNS] + nm.mu_y[kNS], -kLnTen, kLnTen));
-  conserve(nm, y0, y1);
+  *T1 = apply_u(T0, 0.0f, decode_u(o[NS] * nm.sd_y[NS] + nm.mu_y[NS], -kLnTen, kLnTen));
+  conserve<NS>(nm, y0, y1);
 }
 
 // ------------------------------------------------------------------ training kernels
 
-// gather + encode a batch: Xn [B][16] (standardised features, zero padded), Tn [B][10]
-// (standardised target encodings, if Yt), Raw [B][20] = (Y0, T0, Y1, T1).  X rows are
-// (T, p, dt, Y0[ns]); Yt rows are (Y1[ns], T1), the state after dt.
+// X rows are (T, p, dt, Y0[ns]); Yt rows are (Y1[ns], T1), the state after dt.
+template <int NS>
 __device__ __forceinline__ void target_encodings(const float* xr, const float* yr, float* a) {
 #pragma unroll
-  for (int k = 0; k < kNS; ++k) a[k] = encode(log_ratio(yr[k], fmaxf(xr[3 + k], 0.0f), kEps));
-  a[kNS] = encode(log_ratio(yr[kNS], xr[0], 0.0f));
+  for (int k = 0; k < NS; ++k) a[k] = encode(log_ratio(yr[k], fmaxf(xr[3 + k], 0.0f), kEps));
+  a[NS] = encode(log_ratio(yr[NS], xr[0], 0.0f));
 }
 
-__global__ void batch_kernel(const float* X, const float* Yt, const int* idx, int B, const Norm* nm, float* Xn,
+// gather + encode a batch: Xn [B][kKIn] (standardised features, zero padded), Tn [B][kNTgt]
+// (standardised target encodings, if Yt), Raw [B][kRaw] = (Y0, T0, Y1, T1)
+template <int NS>
+__global__ void batch_kernel(const float* X, const float* Yt, const int* idx, int B, const Norm<NS>* nm, float* Xn,
                              float* Tn, float* Raw) {
+  using D = Dims<NS>;
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= B) return;
   const long long i = idx ? idx[b] : b;
-  const float* xr = X + i * kNIn;
-  float y0[kNS], x[kNIn];
+  const float* xr = X + i * D::kNIn;
+  float y0[NS], x[D::kNIn];
 #pragma unroll
-  for (int k = 0; k < kNS; ++k) y0[k] = xr[3 + k];
-  features(xr[0], xr[1], logf(xr[2]), y0, x);
+  for (int k = 0; k < NS; ++k) y0[k] = xr[3 + k];
+  features<NS>(xr[0], xr[1], logf(xr[2]), y0, x);
 #pragma unroll
-  for (int j = 0; j < kKIn; ++j) Xn[b * kKIn + j] = j < kNIn ? (x[j] - nm->mu_x[j]) / nm->sd_x[j] : 0.0f;
+  for (int j = 0; j < D::kKIn; ++j) Xn[b * D::kKIn + j] = j < D::kNIn ? (x[j] - nm->mu_x[j]) / nm->sd_x[j] : 0.0f;
   if (!Yt) return;
-  const float* yr = Yt + i * kNTgt;
-  float a[kNTgt];
-  target_encodings(xr, yr, a);
+  const float* yr = Yt + i * D::kNTgt;
+  float a[D::kNTgt];
+  target_encodings<NS>(xr, yr, a);
 #pragma unroll
-  for (int j = 0; j < kNTgt; ++j) Tn[b * kNTgt + j] = (a[j] - nm->mu_y[j]) / nm->sd_y[j];
+  for (int j = 0; j < D::kNTgt; ++j) Tn[b * D::kNTgt + j] = (a[j] - nm->mu_y[j]) / nm->sd_y[j];
 #pragma unroll
-  for (int k = 0; k < kNS; ++k) {
-    Raw[b * kRaw + k] = y0[k];
-    Raw[b * kRaw + kNS + 1 + k] = yr[k];
+  for (int k = 0; k < NS; ++k) {
+    Raw[b * D::kRaw + k] = y0[k];
+    Raw[b * D::kRaw + NS + 1 + k] = yr[k];
   }
-  Raw[b * kRaw + kNS] = xr[0];
-  Raw[b * kRaw + 2 * kNS + 1] = yr[kNS];
+  Raw[b * D::kRaw + NS] = xr[0];
+  Raw[b * D::kRaw + 2 * NS + 1] = yr[NS];
 }
 
 // relative error of the state the gate would write: max over species of |Y1' - Y1| / max(|Y1|, eps)
 // and |T1' - T1| / T1
-__device__ __forceinline__ float state_error(const Norm& nm, const float* o, const float* raw) {
-  float y1[kNS], T1;
-  decode_state(nm, o, raw, raw[kNS], y1, &T1);
+template <int NS>
+__device__ __forceinline__ float state_error(const Norm<NS>& nm, const float* o, const float* raw) {
+  float y1[NS], T1;
+  decode_state<NS>(nm, o, raw, raw[NS], y1, &T1);
   float E = 0.0f;
 #pragma unroll
-  for (int k = 0; k < kNS; ++k) {
-    const float t = raw[kNS + 1 + k];
+  for (int k = 0; k < NS; ++k) {
+    const float t = raw[NS + 1 + k];
     E = fmaxf(E, fabsf(y1[k] - t) / fmaxf(fabsf(t), kEps));
   }
-  const float Tt = raw[2 * kNS + 1];
+  const float Tt = raw[2 * NS + 1];
   return fmaxf(E, fabsf(T1 - Tt) / Tt);
 }
 
 // loss and its gradient at the output layer: MSE of the standardised target encodings plus
 // err_weight * (o_err - e*)^2 with e* = log10(state error + 1e-12) (no gradient through e*)
-__global__ void loss_kernel(const float* Z5, const float* Tn, const float* Raw, int B, const Norm* nm,
+template <int NS>
+__global__ void loss_kernel(const float* Z5, const float* Tn, const float* Raw, int B, const Norm<NS>* nm,
                             float err_weight, float* dZ5, float* loss) {
+  using D = Dims<NS>;
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   float l = 0.0f;
   if (b < B) {
-    const float* o = Z5 + b * kNOut;
-    for (int j = 0; j < kNTgt; ++j) {
-      const float d = o[j] - Tn[b * kNTgt + j];
+    const float* o = Z5 + b * D::kNOut;
+    for (int j = 0; j < D::kNTgt; ++j) {
+      const float d = o[j] - Tn[b * D::kNTgt + j];
       l += d * d;
-      dZ5[b * kNOut + j] = 2.0f * d / B;
+      dZ5[b * D::kNOut + j] = 2.0f * d / B;
     }
-    const float es = log10f(state_error(*nm, o, Raw + b * kRaw) + 1e-12f);
-    const float de = o[kNS + 1] - es;
+    const float es = log10f(state_error<NS>(*nm, o, Raw + b * D::kRaw) + 1e-12f);
+    const float de = o[NS + 1] - es;
     l += err_weight * de * de;
-    dZ5[b * kNOut + kNS + 1] = 2.0f * err_weight * de / B;
+    dZ5[b * D::kNOut + NS + 1] = 2.0f * err_weight * de / B;
   }
   __shared__ float red[256];
   red[threadIdx.x] = l;
@@ -294,6 +316,8 @@ __global__ void bias_grad_kernel(const float* dZ, int B, int N, float* db) {
   atomicAdd(&db[n], s);
 }
 
+// AdamW (Adam moments with bias correction c1 = 1 - b1^t, c2 = 1 - b2^t, and weight decay
+// decoupled from the adaptive step, scaled by the scheduled learning rate lr)
 __global__ void adamw_kernel(float* w, const float* g, float* m, float* v, int n, float lr, float b1, float b2,
                              float eps, float wd, float c1, float c2) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -313,32 +337,34 @@ __device__ __forceinline__ unsigned int order_key(float v) {
   return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
 }
 
+template <int NS>
 __global__ void stats_kernel(const float* X, const float* Yt, long long n, double* acc, unsigned int* mm) {
-  constexpr int NT = kNIn + kNTgt;
+  using D = Dims<NS>;
+  constexpr int NT = D::kNIn + D::kNTgt;
   double s[NT], q[NT];
   for (int j = 0; j < NT; ++j) s[j] = q[j] = 0.0;
-  unsigned int lo[kNIn], hi[kNIn];
-  for (int j = 0; j < kNIn; ++j) {
+  unsigned int lo[D::kNIn], hi[D::kNIn];
+  for (int j = 0; j < D::kNIn; ++j) {
     lo[j] = 0xFFFFFFFFu;
     hi[j] = 0u;
   }
   for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
        i += static_cast<long long>(gridDim.x) * blockDim.x) {
-    const float* xr = X + i * kNIn;
-    const float* yr = Yt + i * kNTgt;
-    float y0[kNS], x[kNIn], a[kNTgt];
-    for (int k = 0; k < kNS; ++k) y0[k] = xr[3 + k];
-    features(xr[0], xr[1], logf(xr[2]), y0, x);
-    target_encodings(xr, yr, a);
-    for (int j = 0; j < kNIn; ++j) {
+    const float* xr = X + i * D::kNIn;
+    const float* yr = Yt + i * D::kNTgt;
+    float y0[NS], x[D::kNIn], a[D::kNTgt];
+    for (int k = 0; k < NS; ++k) y0[k] = xr[3 + k];
+    features<NS>(xr[0], xr[1], logf(xr[2]), y0, x);
+    target_encodings<NS>(xr, yr, a);
+    for (int j = 0; j < D::kNIn; ++j) {
       s[j] += x[j];
       q[j] += static_cast<double>(x[j]) * x[j];
     }
-    for (int j = 0; j < kNTgt; ++j) {
-      s[kNIn + j] += a[j];
-      q[kNIn + j] += static_cast<double>(a[j]) * a[j];
+    for (int j = 0; j < D::kNTgt; ++j) {
+      s[D::kNIn + j] += a[j];
+      q[D::kNIn + j] += static_cast<double>(a[j]) * a[j];
     }
-    for (int j = 0; j < kNIn; ++j) {
+    for (int j = 0; j < D::kNIn; ++j) {
       lo[j] = min(lo[j], order_key(x[j]));
       hi[j] = max(hi[j], order_key(x[j]));
     }
@@ -347,16 +373,18 @@ __global__ void stats_kernel(const float* X, const float* Yt, long long n, doubl
     atomicAdd(&acc[j], s[j]);
     atomicAdd(&acc[NT + j], q[j]);
   }
-  for (int j = 0; j < kNIn; ++j) {
+  for (int j = 0; j < D::kNIn; ++j) {
     atomicMin(&mm[j], lo[j]);
-    atomicMax(&mm[kNIn + j], hi[j]);
+    atomicMax(&mm[D::kNIn + j], hi[j]);
   }
 }
 
 // ------------------------------------------------------------------ inference blob
 
 // BF16 weights into the shared-memory image (K-major core matrices), biases and Norm after them
-__global__ void pack_blob_kernel(const float* params, const Norm* nm, unsigned char* blob) {
+template <int NS>
+__global__ void pack_blob_kernel(const float* params, const Norm<NS>* nm, unsigned char* blob) {
+  using D = Dims<NS>;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int nt = gridDim.x * blockDim.x;
   auto put = [&](int base, const float* W, int rows, int rows_valid, int K, int K_valid) {
@@ -366,34 +394,32 @@ __global__ void pack_blob_kernel(const float* params, const Norm* nm, unsigned c
       *reinterpret_cast<__nv_bfloat16*>(blob + base + tc::kmajor_offset(r, k, K)) = __float2bfloat16_rn(v);
     }
   };
-  put(bW1, params + oW1, kH, kH, kKIn, kNIn);
-  put(bW2, params + oW2, kH, kH, kH, kH);
-  put(bW3, params + oW3, kH, kH, kH, kH);
-  put(bW4, params + oW4, kH, kH, kH, kH);
-  put(bW5, params + oW5, kNOutPad, kNOut, kH, kH);
-  float* bias = reinterpret_cast<float*>(blob + bBias);
-  for (int i = t; i < 4 * kH + kNOutPad; i += nt) {
+  put(D::bW1, params + D::oW1, kH, kH, D::kKIn, D::kNIn);
+  put(D::bW2, params + D::oW2, kH, kH, kH, kH);
+  put(D::bW3, params + D::oW3, kH, kH, kH, kH);
+  put(D::bW4, params + D::oW4, kH, kH, kH, kH);
+  put(D::bW5, params + D::oW5, D::kNOutPad, D::kNOut, kH, kH);
+  float* bias = reinterpret_cast<float*>(blob + D::bBias);
+  for (int i = t; i < 4 * kH + D::kNOutPad; i += nt) {
     float v;
     if (i < 4 * kH) {
       const int l = i / kH, n = i % kH;
-      const int ob = l == 0 ? oB1 : (l == 1 ? oB2 : (l == 2 ? oB3 : oB4));
-      v = params[ob + n];
+      v = params[D::bo(l) + n];
     } else {
       const int n = i - 4 * kH;
-      v = n < kNOut ? params[oB5 + n] : 0.0f;
+      v = n < D::kNOut ? params[D::oB5 + n] : 0.0f;
     }
     bias[i] = v;
   }
   const int* src = reinterpret_cast<const int*>(nm);
-  int* dst = reinterpret_cast<int*>(blob + bNorm);
-  for (int i = t; i < static_cast<int>(sizeof(Norm) / 4); i += nt) dst[i] = src[i];
+  int* dst = reinterpret_cast<int*>(blob + D::bNorm);
+  for (int i = t; i < static_cast<int>(sizeof(Norm<NS>) / 4); i += nt) dst[i] = src[i];
 }
 
 // ------------------------------------------------------------------ fused inference + gate
 
 struct GatedArgs {
-  const unsigned char* mech;      // chemistry tables (T(e) for the gate)
-  unsigned mech_bytes;
+  const unsigned char* mech;      // chemistry tables (T(e) for the gate), read through L1
   const unsigned char* sblob;     // packed surrogate image
   float* T;
   float* p;
@@ -413,20 +439,25 @@ struct GatedArgs {
 
 constexpr int kInferThreads = 256;   // warps w and w + 4 share TMEM lanes 32 (w % 4).. and split the columns
 
+template <int NS>
+__host__ __device__ constexpr unsigned infer_smem_bytes() {
+  return ((blob_bytes<NS>() + 1023) & ~1023) + kH * Dims<NS>::kKIn * 2 + kH * kH * 2;
+}
+
+template <int NS>
 __global__ void __launch_bounds__(kInferThreads, 1) surrogate_infer_kernel(const GatedArgs a) {
+  using D = Dims<NS>;
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ uint64_t bar_s, bar_m, bar_mma;
+  __shared__ uint64_t bar_s, bar_mma;
   __shared__ uint32_t s_taddr;
-  // shared-memory image: [surrogate blob][mechanism blob][X tile 128x16][H tile 128x128]
+  // shared-memory image: [surrogate blob][X tile 128 x kKIn][H tile 128 x 128]
   unsigned char* sS = smem;
-  unsigned char* sM = smem + ((kBlobBytes + 1023) & ~1023);
-  unsigned char* sX = sM + ((a.mech_bytes + 1023) & ~1023);
-  unsigned char* sHt = sX + kH * kKIn * 2;
-  if (!stage_to_smem(sS, a.sblob, kBlobBytes, &bar_s, a.status)) return;
-  if (!stage_to_smem(sM, a.mech, a.mech_bytes, &bar_m, a.status)) return;
-  const MechView m = make_view(sM);
-  const Norm& nm = *reinterpret_cast<const Norm*>(sS + bNorm);
-  const float* bias = reinterpret_cast<const float*>(sS + bBias);
+  unsigned char* sX = smem + ((blob_bytes<NS>() + 1023) & ~1023);
+  unsigned char* sHt = sX + kH * D::kKIn * 2;
+  if (!stage_to_smem(sS, a.sblob, blob_bytes<NS>(), &bar_s, a.status)) return;
+  const MechView m = make_view(a.mech);   // only the gate's T(e) reads it: through L1
+  const Norm<NS>& nm = *reinterpret_cast<const Norm<NS>*>(sS + D::bNorm);
+  const float* bias = reinterpret_cast<const float*>(sS + D::bBias);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int t = threadIdx.x & (kH - 1);   // tile row of this thread (TMEM lane)
   const bool rowner = threadIdx.x < kH;   // threads 0..127 own the rows (features, outputs, gate)
@@ -446,8 +477,8 @@ __global__ void __launch_bounds__(kInferThreads, 1) surrogate_infer_kernel(const
   for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
     const long long i = tile * kH + t;
     const bool valid = rowner && i < a.n;
-    float y[kNS], T = 0.0f, rho = 1.0f, e = 0.0f;
-    float x[kNIn];
+    float y[NS], T = 0.0f, rho = 1.0f, e = 0.0f;
+    float x[D::kNIn];
     bool inbox = valid;
     if (valid) {
       T = a.T[i];
@@ -455,39 +486,41 @@ __global__ void __launch_bounds__(kInferThreads, 1) surrogate_infer_kernel(const
       e = a.e[i];
       double sw = 0.0;
 #pragma unroll
-      for (int k = 0; k < kNS; ++k) {
+      for (int k = 0; k < NS; ++k) {
         y[k] = a.Y[k * a.ld + i];
         sw += static_cast<double>(y[k]) * m.e64[k * 8 + 6];
         inbox = inbox && y[k] >= -a.atol;
       }
       const float p = static_cast<float>(static_cast<double>(rho) * kR * T * sw);
-      features(T, p, lndt, y, x);
+      features<NS>(T, p, lndt, y, x);
 #pragma unroll
-      for (int j = 0; j < kNIn; ++j) {   // the box with a margin of 1e-3 of each range (rounding)
+      for (int j = 0; j < D::kNIn; ++j) {   // the box with a margin of 1e-3 of each range (rounding)
         const float mg = 1e-3f * (nm.hi_x[j] - nm.lo_x[j]);
         inbox = inbox && x[j] >= nm.lo_x[j] - mg && x[j] <= nm.hi_x[j] + mg;
       }
     } else {
 #pragma unroll
-      for (int k = 0; k < kNS; ++k) y[k] = 0.0f;
+      for (int k = 0; k < NS; ++k) y[k] = 0.0f;
 #pragma unroll
-      for (int j = 0; j < kNIn; ++j) x[j] = nm.mu_x[j];
+      for (int j = 0; j < D::kNIn; ++j) x[j] = nm.mu_x[j];
     }
-    // standardised features -> BF16 row t of the X tile
+    // standardised features -> BF16 row t of the X tile, 8 columns (16 bytes) at a time
     if (rowner) {
-      uint32_t w[8];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const int c0 = 2 * j, c1 = 2 * j + 1;
-        const float v0 = c0 < kNIn ? (x[c0] - nm.mu_x[c0]) / nm.sd_x[c0] : 0.0f;
-        const float v1 = c1 < kNIn ? (x[c1] - nm.mu_x[c1]) / nm.sd_x[c1] : 0.0f;
-        const __nv_bfloat162 b2 = __floats2bfloat162_rn(v0, v1);
-        w[j] = *reinterpret_cast<const uint32_t*>(&b2);
+      for (int c8 = 0; c8 < D::kKIn; c8 += 8) {
+        uint32_t w[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int c0 = c8 + 2 * j, c1 = c8 + 2 * j + 1;
+          const float v0 = c0 < D::kNIn ? (x[c0] - nm.mu_x[c0]) / nm.sd_x[c0] : 0.0f;
+          const float v1 = c1 < D::kNIn ? (x[c1] - nm.mu_x[c1]) / nm.sd_x[c1] : 0.0f;
+          const __nv_bfloat162 b2 = __floats2bfloat162_rn(v0, v1);
+          w[j] = *reinterpret_cast<const uint32_t*>(&b2);
+        }
+        *reinterpret_cast<uint4*>(sX + tc::kmajor_offset(t, c8, D::kKIn)) = make_uint4(w[0], w[1], w[2], w[3]);
       }
-      *reinterpret_cast<uint4*>(sX + tc::kmajor_offset(t, 0, kKIn)) = make_uint4(w[0], w[1], w[2], w[3]);
-      *reinterpret_cast<uint4*>(sX + tc::kmajor_offset(t, 8, kKIn)) = make_uint4(w[4], w[5], w[6], w[7]);
     }
-    float o[kNOutPad];
+    float o[D::kNOutPad];
 #pragma unroll 1
     for (int layer = 0; layer < 5; ++layer) {
       tc::fence_async_smem();
@@ -495,10 +528,10 @@ __global__ void __launch_bounds__(kInferThreads, 1) surrogate_infer_kernel(const
       __syncthreads();
       if (threadIdx.x == 0) {
         tc::fence_after_sync();
-        const int K = layer == 0 ? kKIn : kH;
-        const int N = layer == 4 ? kNOutPad : kH;
+        const int K = layer == 0 ? D::kKIn : kH;
+        const int N = layer == 4 ? D::kNOutPad : kH;
         const unsigned char* Asm = layer == 0 ? sX : sHt;
-        const int wb = layer == 0 ? bW1 : (layer == 1 ? bW2 : (layer == 2 ? bW3 : (layer == 3 ? bW4 : bW5)));
+        const int wb = layer == 0 ? D::bW1 : (layer == 1 ? D::bW2 : (layer == 2 ? D::bW3 : (layer == 3 ? D::bW4 : D::bW5)));
         const uint32_t idesc = tc::idesc_bf16_f32(kH, N);
         for (int kk = 0; kk < K / 16; ++kk) {
           const uint64_t ad = tc::smem_desc(tc::smem_u32(Asm) + kk * 256, 128, (K / 8) * 128);
@@ -528,24 +561,28 @@ __global__ void __launch_bounds__(kInferThreads, 1) surrogate_infer_kernel(const
           *reinterpret_cast<uint4*>(sHt + tc::kmajor_offset(t, n0 + 8, kH)) = make_uint4(w[4], w[5], w[6], w[7]);
         }
       } else if (rowner) {
-        tc::tmem_ld16(lane_addr, o);
 #pragma unroll
-        for (int j = 0; j < kNOutPad; ++j) o[j] += bias[4 * kH + j];
+        for (int c16 = 0; c16 < D::kNOutPad; c16 += 16) {
+          float v[16];
+          tc::tmem_ld16(lane_addr + c16, v);
+#pragma unroll
+          for (int j = 0; j < 16; ++j) o[c16 + j] = v[j] + bias[4 * kH + c16 + j];
+        }
       }
     }
     if (!ok) break;
     if (valid) {
       if (a.out) {
 #pragma unroll
-        for (int j = 0; j < kNOut; ++j) a.out[i * kNOut + j] = o[j];
+        for (int j = 0; j < D::kNOut; ++j) a.out[i * D::kNOut + j] = o[j];
       }
-      bool acc = inbox && (o[kNS + 1] <= a.gate_log10);
+      bool acc = inbox && (o[NS + 1] <= a.gate_log10);
       if (acc) {
-        float yn[kNS], T1;
-        decode_state(nm, o, y, T, yn, &T1);
+        float yn[NS], T1;
+        decode_state<NS>(nm, o, y, T, yn, &T1);
         double sdy = 0.0;
 #pragma unroll
-        for (int k = 0; k < kNS; ++k) {
+        for (int k = 0; k < NS; ++k) {
           sdy += static_cast<double>(yn[k]) - static_cast<double>(y[k]);
           acc = acc && isfinite(yn[k]) && yn[k] >= -a.atol && yn[k] <= 1.0f + 1e-6f;
         }
@@ -553,12 +590,12 @@ __global__ void __launch_bounds__(kInferThreads, 1) surrogate_infer_kernel(const
         if (acc) {
           bool okT;
           const double Tg = T1;
-          const double Tn = temperature_from_energy<kNS>(m, yn, static_cast<double>(e), Tg, &okT);
+          const double Tn = temperature_from_energy<NS>(m, yn, static_cast<double>(e), Tg, &okT);
           acc = okT && fabs(Tn - Tg) <= 1e-4 * Tn;
           if (acc) {
             double sw = 0.0;
 #pragma unroll
-            for (int k = 0; k < kNS; ++k) {
+            for (int k = 0; k < NS; ++k) {
               a.Y[k * a.ld + i] = yn[k];
               sw += static_cast<double>(yn[k]) * m.e64[k * 8 + 6];
             }
@@ -586,19 +623,18 @@ __global__ void __launch_bounds__(kInferThreads, 1) surrogate_infer_kernel(const
   if (lane == 0 && c_acc) atomicAdd(a.n_accepted, c_acc);
 }
 
-size_t infer_smem_bytes(unsigned mech_bytes) {
-  return ((kBlobBytes + 1023) & ~1023) + ((mech_bytes + 1023) & ~1023) + kH * kKIn * 2 + kH * kH * 2;
-}
-
 // ====================================================================== host side
 
+// State of one context's surrogate; the shapes follow its species count ns (9 or 53).
 struct State {
-  float* params = nullptr;   // [kNParams] FP32 masters
+  int ns = 0;
+  int nparams = 0;
+  float* params = nullptr;   // [nparams] FP32 masters
   float* grads = nullptr;
   float* m = nullptr;
   float* v = nullptr;
-  Norm* norm = nullptr;      // device
-  Norm hnorm{};              // host copy
+  void* norm = nullptr;      // device Norm<ns>
+  std::vector<unsigned char> hnorm;   // host copy of the Norm<ns> bytes
   unsigned char* blob = nullptr;
   bool blob_dirty = true;
   unsigned long long* n_acc = nullptr;
@@ -642,16 +678,19 @@ void free_state(State* s) {
   delete s;
 }
 
+template <int NS>
 int ensure_batch(State* s, int B) {
+  using D = Dims<NS>;
   if (s->cap >= B) return CHEM_OK;
   free_batch(s);
   const size_t b = static_cast<size_t>(B);
-  bool ok = cudaMalloc(&s->Xn, sizeof(float) * b * kKIn) == cudaSuccess &&
-            cudaMalloc(&s->Tn, sizeof(float) * b * kNTgt) == cudaSuccess &&
-            cudaMalloc(&s->Raw, sizeof(float) * b * kRaw) == cudaSuccess &&
+  bool ok = cudaMalloc(&s->Xn, sizeof(float) * b * D::kKIn) == cudaSuccess &&
+            cudaMalloc(&s->Tn, sizeof(float) * b * D::kNTgt) == cudaSuccess &&
+            cudaMalloc(&s->Raw, sizeof(float) * b * D::kRaw) == cudaSuccess &&
             cudaMalloc(&s->dZ, sizeof(float) * b * kH) == cudaSuccess &&
             cudaMalloc(&s->dA, sizeof(float) * b * kH) == cudaSuccess;
-  for (int l = 0; l < 5 && ok; ++l) ok = cudaMalloc(&s->Z[l], sizeof(float) * b * (l < 4 ? kH : kNOut)) == cudaSuccess;
+  for (int l = 0; l < 5 && ok; ++l)
+    ok = cudaMalloc(&s->Z[l], sizeof(float) * b * (l < 4 ? kH : D::kNOut)) == cudaSuccess;
   for (int l = 0; l < 4 && ok; ++l) ok = cudaMalloc(&s->A[l], sizeof(float) * b * kH) == cudaSuccess;
   if (!ok) {
     free_batch(s);
@@ -692,45 +731,46 @@ GemmArgs gemm(const float* A, long long sam, long long sak, const float* B, long
   return g;
 }
 
-constexpr int kWo[5] = {oW1, oW2, oW3, oW4, oW5};
-constexpr int kBo[5] = {oB1, oB2, oB3, oB4, oB5};
-constexpr int kIn[5] = {kNIn, kH, kH, kH, kH};
-constexpr int kOut[5] = {kH, kH, kH, kH, kNOut};
 constexpr int kEpiStore = 0, kEpiBias = 1, kEpiBiasGelu = 2, kEpiAtomic = 3;   // as in mlp.cu
 
-// forward of a batch of B standardised rows Xn [B][16] through the GEMM kernels: Z_l (pre-
+// forward of a batch of B standardised rows Xn [B][kKIn] through the GEMM kernels: Z_l (pre-
 // activation) and A_l = gelu(Z_l) for the hidden layers, Z_5 = the outputs
+template <int NS>
 int forward(State* s, int B, cudaStream_t st) {
+  using D = Dims<NS>;
   int r = 0;
   for (int l = 0; l < 5 && !r; ++l) {
     const float* in = l == 0 ? s->Xn : s->A[l - 1];
-    const long long ldin = l == 0 ? kKIn : kH;
-    r = launch_gemm(gemm(in, ldin, 1, s->params + kWo[l], kIn[l], 1, s->Z[l], kOut[l], B, kOut[l], kIn[l],
-                         l < 4 ? kEpiBiasGelu : kEpiBias, s->params + kBo[l], l < 4 ? s->A[l] : nullptr, s->status),
+    const long long ldin = l == 0 ? D::kKIn : kH;
+    r = launch_gemm(gemm(in, ldin, 1, s->params + D::wo(l), D::in(l), 1, s->Z[l], D::out(l), B, D::out(l), D::in(l),
+                         l < 4 ? kEpiBiasGelu : kEpiBias, s->params + D::bo(l), l < 4 ? s->A[l] : nullptr, s->status),
                     1, st);
   }
   return r;
 }
 
 // loss gradient of the batch into s->grads (zeroed here); the batch loss is added to s->loss
+template <int NS>
 int backward(State* s, int B, float err_weight, cudaStream_t st) {
+  using D = Dims<NS>;
   int r = 0;
-  cudaMemsetAsync(s->grads, 0, sizeof(float) * kNParams, st);
-  loss_kernel<<<(B + 255) / 256, 256, 0, st>>>(s->Z[4], s->Tn, s->Raw, B, s->norm, err_weight, s->dZ, s->loss);
+  cudaMemsetAsync(s->grads, 0, sizeof(float) * D::kNParams, st);
+  loss_kernel<NS><<<(B + 255) / 256, 256, 0, st>>>(s->Z[4], s->Tn, s->Raw, B, static_cast<const Norm<NS>*>(s->norm),
+                                                    err_weight, s->dZ, s->loss);
   const int ks = B >= 2048 ? 16 : (B >= 512 ? 4 : 1);   // batch split of the weight gradients
   for (int l = 4; l >= 0 && !r; --l) {
-    const int nin = kIn[l], nout = kOut[l];
+    const int nin = D::in(l), nout = D::out(l);
     const float* inact = l == 0 ? s->Xn : s->A[l - 1];
-    const long long ldin = l == 0 ? kKIn : kH;
+    const long long ldin = l == 0 ? D::kKIn : kH;
     // dW[out][in] = sum_b dZ[b][out] in[b][in]
-    r = launch_gemm(gemm(s->dZ, 1, nout, inact, 1, ldin, s->grads + kWo[l], nin, nout, nin, B, kEpiAtomic, nullptr,
-                         nullptr, s->status),
+    r = launch_gemm(gemm(s->dZ, 1, nout, inact, 1, ldin, s->grads + D::wo(l), nin, nout, nin, B, kEpiAtomic,
+                         nullptr, nullptr, s->status),
                     ks, st);
     if (r) break;
-    bias_grad_kernel<<<64, 128, 0, st>>>(s->dZ, B, nout, s->grads + kBo[l]);
+    bias_grad_kernel<<<64, 128, 0, st>>>(s->dZ, B, nout, s->grads + D::bo(l));
     if (l == 0) break;
     // dA[b][in] = sum_out dZ[b][out] W[out][in], then dZ_{l-1} = dA * gelu'(Z_{l-1})
-    r = launch_gemm(gemm(s->dZ, nout, 1, s->params + kWo[l], 1, nin, s->dA, nin, B, nin, nout, kEpiStore, nullptr,
+    r = launch_gemm(gemm(s->dZ, nout, 1, s->params + D::wo(l), 1, nin, s->dA, nin, B, nin, nout, kEpiStore, nullptr,
                          nullptr, s->status),
                     1, st);
     if (r) break;
@@ -765,10 +805,17 @@ using namespace chem::sg;
 
 namespace {
 
+// species counts the surrogate is compiled for
+bool surrogate_ns(int ns) { return ns == 9 || ns == 53; }
+
+// fn<NS>(args...) for the compiled species counts
+#define SG_DISPATCH(ns, fn, ...) \
+  ((ns) == 9 ? fn<9>(__VA_ARGS__) : ((ns) == 53 ? fn<53>(__VA_ARGS__) : CHEM_EUNSUPPORTED))
+
 // Orthonormal basis of the complement of span{W .* (nu_r - nu_f)_r}: the directions of Y that no
-// reaction changes (element and total-mass conservation).  Returns the number of directions.
-int conserved_directions(int ns, int nr, const double* W, const int8_t* nuf, const int8_t* nur,
-                         float C[kMaxCons][kNS]) {
+// reaction changes (element and total-mass conservation).  Writes up to kMaxCons rows of ns into
+// C (row-major) and returns the number of directions.
+int conserved_directions(int ns, int nr, const double* W, const int8_t* nuf, const int8_t* nur, float* C) {
   std::vector<std::vector<double>> Q;
   auto orth = [&](std::vector<double>& v) {
     for (int pass = 0; pass < 2; ++pass)
@@ -794,7 +841,6 @@ int conserved_directions(int ns, int nr, const double* W, const int8_t* nuf, con
       Q.push_back(v);
     }
   }
-  const size_t nreact = Q.size();
   int m = 0;
   for (int j = 0; j < ns; ++j) {
     std::vector<double> v(ns, 0.0);
@@ -804,11 +850,10 @@ int conserved_directions(int ns, int nr, const double* W, const int8_t* nuf, con
       for (double& x : v) x /= nrm;
       Q.push_back(v);
       if (m < kMaxCons)
-        for (int k = 0; k < ns; ++k) C[m][k] = static_cast<float>(v[k]);
+        for (int k = 0; k < ns; ++k) C[m * ns + k] = static_cast<float>(v[k]);
       ++m;
     }
   }
-  (void)nreact;
   return m;
 }
 
@@ -820,9 +865,14 @@ int fail_cuda(cudaError_t e, const char* what) {
 
 State* get_state(chem_ctx* ctx) { return ctx ? ctx_surrogate(ctx) : nullptr; }
 
+template <int NS>
+Norm<NS>& host_norm(State* s) {
+  return *reinterpret_cast<Norm<NS>*>(s->hnorm.data());
+}
+
 int upload_norm(State* s, cudaStream_t st) {
   s->blob_dirty = true;
-  int rc = fail_cuda(cudaMemcpyAsync(s->norm, &s->hnorm, sizeof(Norm), cudaMemcpyHostToDevice, st), "norm");
+  int rc = fail_cuda(cudaMemcpyAsync(s->norm, s->hnorm.data(), s->hnorm.size(), cudaMemcpyHostToDevice, st), "norm");
   return rc ? rc : fail_cuda(cudaStreamSynchronize(st), "norm");
 }
 
@@ -838,51 +888,59 @@ int device_status(State* s, cudaStream_t st) {
   return CHEM_OK;
 }
 
+template <int NS>
 int launch_infer(chem_ctx* ctx, State* s, const GatedArgs& g0, cudaStream_t st) {
   if (s->blob_dirty) {
-    pack_blob_kernel<<<64, 256, 0, st>>>(s->params, s->norm, s->blob);
+    pack_blob_kernel<NS><<<64, 256, 0, st>>>(s->params, static_cast<const Norm<NS>*>(s->norm), s->blob);
     s->blob_dirty = false;
   }
   GatedArgs g = g0;
-  g.mech = ctx_blob(ctx, &g.mech_bytes);
+  unsigned mech_bytes = 0;
+  g.mech = ctx_blob(ctx, &mech_bytes);
   g.sblob = s->blob;
   g.n_accepted = s->n_acc;
   g.status = s->status;
-  const size_t smem = infer_smem_bytes(g.mech_bytes);
-  cudaFuncSetAttribute(surrogate_infer_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  constexpr unsigned smem = infer_smem_bytes<NS>();
+  cudaFuncSetAttribute(surrogate_infer_kernel<NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   int dev = 0, sms = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const long long tiles = (g.n + kH - 1) / kH;
   const int grid = static_cast<int>(tiles < sms ? tiles : sms);
-  surrogate_infer_kernel<<<grid, kInferThreads, smem, st>>>(g);
+  surrogate_infer_kernel<NS><<<grid, kInferThreads, smem, st>>>(g);
   return fail_cuda(cudaGetLastError(), "surrogate kernel");
 }
 
-}  // namespace
-
-extern "C" {
-
-int chem_surrogate_nparams(void) { return kNParams; }
-
-int chem_surrogate_init(chem_ctx* ctx, uint64_t seed) {
-  if (!ctx) return CHEM_EINVAL;
+int context_ns(chem_ctx* ctx) {
   int ns, nr;
   const double* W;
   const int8_t *nuf, *nur;
   ctx_mech_host(ctx, &ns, &nr, &W, &nuf, &nur);
-  if (ns != kNS) return CHEM_EUNSUPPORTED;
-  Norm nm{};
-  const int m = conserved_directions(ns, nr, W, nuf, nur, nm.C);
+  return ns;
+}
+
+template <int NS>
+int surrogate_init_t(chem_ctx* ctx, uint64_t seed) {
+  using D = Dims<NS>;
+  int ns, nr;
+  const double* W;
+  const int8_t *nuf, *nur;
+  ctx_mech_host(ctx, &ns, &nr, &W, &nuf, &nur);
+  Norm<NS> nm{};
+  const int m = conserved_directions(ns, nr, W, nuf, nur, &nm.C[0][0]);
   if (m > kMaxCons) return CHEM_EUNSUPPORTED;
   State* s = get_state(ctx);
   if (!s) {
     s = new State();
-    bool ok = cudaMalloc(&s->params, sizeof(float) * kNParams) == cudaSuccess &&
-              cudaMalloc(&s->grads, sizeof(float) * kNParams) == cudaSuccess &&
-              cudaMalloc(&s->m, sizeof(float) * kNParams) == cudaSuccess &&
-              cudaMalloc(&s->v, sizeof(float) * kNParams) == cudaSuccess &&
-              cudaMalloc(&s->norm, sizeof(Norm)) == cudaSuccess && cudaMalloc(&s->blob, kBlobBytes) == cudaSuccess &&
+    s->ns = NS;
+    s->nparams = D::kNParams;
+    s->hnorm.assign(sizeof(Norm<NS>), 0);
+    bool ok = cudaMalloc(&s->params, sizeof(float) * D::kNParams) == cudaSuccess &&
+              cudaMalloc(&s->grads, sizeof(float) * D::kNParams) == cudaSuccess &&
+              cudaMalloc(&s->m, sizeof(float) * D::kNParams) == cudaSuccess &&
+              cudaMalloc(&s->v, sizeof(float) * D::kNParams) == cudaSuccess &&
+              cudaMalloc(&s->norm, sizeof(Norm<NS>)) == cudaSuccess &&
+              cudaMalloc(&s->blob, blob_bytes<NS>()) == cudaSuccess &&
               cudaMalloc(&s->n_acc, sizeof(unsigned long long)) == cudaSuccess &&
               cudaMalloc(&s->status, sizeof(int)) == cudaSuccess && cudaMalloc(&s->loss, sizeof(float)) == cudaSuccess;
     if (!ok) {
@@ -892,84 +950,82 @@ int chem_surrogate_init(chem_ctx* ctx, uint64_t seed) {
     ctx_set_surrogate(ctx, s);
   }
   // He initialisation of the weights (output layer scaled down), zero biases and moments
-  std::vector<float> h(kNParams, 0.0f);
+  std::vector<float> h(D::kNParams, 0.0f);
   std::mt19937_64 rng(seed);
   for (int l = 0; l < 5; ++l) {
-    std::normal_distribution<float> nd(0.0f, std::sqrt(2.0f / kIn[l]) * (l == 4 ? 0.5f : 1.0f));
-    for (int i = 0; i < kIn[l] * kOut[l]; ++i) h[kWo[l] + i] = nd(rng);
+    std::normal_distribution<float> nd(0.0f, std::sqrt(2.0f / D::in(l)) * (l == 4 ? 0.5f : 1.0f));
+    for (int i = 0; i < D::in(l) * D::out(l); ++i) h[D::wo(l) + i] = nd(rng);
   }
-  int rc = fail_cuda(cudaMemcpy(s->params, h.data(), sizeof(float) * kNParams, cudaMemcpyHostToDevice), "init");
+  int rc = fail_cuda(cudaMemcpy(s->params, h.data(), sizeof(float) * D::kNParams, cudaMemcpyHostToDevice), "init");
   if (rc) return rc;
-  cudaMemset(s->m, 0, sizeof(float) * kNParams);
-  cudaMemset(s->v, 0, sizeof(float) * kNParams);
+  cudaMemset(s->m, 0, sizeof(float) * D::kNParams);
+  cudaMemset(s->v, 0, sizeof(float) * D::kNParams);
   cudaMemset(s->status, 0, sizeof(int));
   s->adam_t = 0;
-  for (int j = 0; j < kNIn; ++j) nm.sd_x[j] = 1.0f;
-  for (int j = 0; j < kNTgt; ++j) nm.sd_y[j] = 1.0f;
-  for (int j = 0; j < kNIn; ++j) {   // empty box: nothing is accepted before training
+  for (int j = 0; j < D::kNIn; ++j) nm.sd_x[j] = 1.0f;
+  for (int j = 0; j < D::kNTgt; ++j) nm.sd_y[j] = 1.0f;
+  for (int j = 0; j < D::kNIn; ++j) {   // empty box: nothing is accepted before training
     nm.lo_x[j] = 1.0f;
     nm.hi_x[j] = -1.0f;
   }
   nm.ncons = m;
-  s->hnorm = nm;
+  host_norm<NS>(s) = nm;
   return upload_norm(s, nullptr);
 }
 
-int chem_surrogate_train(chem_ctx* ctx, const float* X, const float* Yt, int64_t n, const chem_train_cfg* cfg,
-                         float* loss_per_epoch, void* stream) {
-  State* s = get_state(ctx);
-  if (!s || !X || !Yt || !cfg || cfg->epochs < 0 || cfg->batch < 128 || (cfg->batch % 128) || !(cfg->lr > 0) ||
-      n < cfg->batch || n > 0x7fffffffLL || !(cfg->weight_decay >= 0) || !(cfg->err_weight >= 0))
-    return CHEM_EINVAL;
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
+template <int NS>
+int surrogate_train_t(State* s, const float* X, const float* Yt, int64_t n, const chem_train_cfg* cfg,
+                      float* loss_per_epoch, cudaStream_t st) {
+  using D = Dims<NS>;
   const int B = cfg->batch;
-  int rc = ensure_batch(s, B);
+  int rc = ensure_batch<NS>(s, B);
   if (!rc) rc = ensure_idx(s, n);
   if (rc) return rc;
   // normalisation statistics and the training box of this data set
-  constexpr int NT = kNIn + kNTgt;
+  constexpr int NT = D::kNIn + D::kNTgt;
   double* acc = nullptr;
   unsigned int* mm = nullptr;
   if (cudaMalloc(&acc, sizeof(double) * 2 * NT) != cudaSuccess) return CHEM_ENOMEM;
-  if (cudaMalloc(&mm, sizeof(unsigned int) * 2 * kNIn) != cudaSuccess) {
+  if (cudaMalloc(&mm, sizeof(unsigned int) * 2 * D::kNIn) != cudaSuccess) {
     cudaFree(acc);
     return CHEM_ENOMEM;
   }
   cudaMemsetAsync(acc, 0, sizeof(double) * 2 * NT, st);
-  unsigned int init[2 * kNIn];
-  for (int j = 0; j < kNIn; ++j) {
+  unsigned int init[2 * D::kNIn];
+  for (int j = 0; j < D::kNIn; ++j) {
     init[j] = 0xFFFFFFFFu;
-    init[kNIn + j] = 0u;
+    init[D::kNIn + j] = 0u;
   }
   cudaMemcpyAsync(mm, init, sizeof(init), cudaMemcpyHostToDevice, st);
-  stats_kernel<<<304, 128, 0, st>>>(X, Yt, n, acc, mm);
+  stats_kernel<NS><<<304, 128, 0, st>>>(X, Yt, n, acc, mm);
   double hacc[2 * NT];
-  unsigned int hmm[2 * kNIn];
+  unsigned int hmm[2 * D::kNIn];
   cudaMemcpyAsync(hacc, acc, sizeof(hacc), cudaMemcpyDeviceToHost, st);
   cudaMemcpyAsync(hmm, mm, sizeof(hmm), cudaMemcpyDeviceToHost, st);
   rc = fail_cuda(cudaStreamSynchronize(st), "statistics");
   cudaFree(acc);
   cudaFree(mm);
   if (rc) return rc;
-  Norm& nm = s->hnorm;
+  Norm<NS>& nm = host_norm<NS>(s);
   for (int j = 0; j < NT; ++j) {
     const double mu = hacc[j] / static_cast<double>(n);
     const double var = std::fmax(hacc[NT + j] / static_cast<double>(n) - mu * mu, 0.0);
     const float sd = static_cast<float>(std::sqrt(var) > 1e-12 ? std::sqrt(var) : 1.0);
     if (!std::isfinite(mu) || !std::isfinite(var)) return CHEM_EINVAL;   // non-finite samples
-    if (j < kNIn) {
+    if (j < D::kNIn) {
       nm.mu_x[j] = static_cast<float>(mu);
       nm.sd_x[j] = sd;
     } else {
-      nm.mu_y[j - kNIn] = static_cast<float>(mu);
-      nm.sd_y[j - kNIn] = sd;
+      nm.mu_y[j - D::kNIn] = static_cast<float>(mu);
+      nm.sd_y[j - D::kNIn] = sd;
     }
   }
-  for (int j = 0; j < kNIn; ++j) {
+  for (int j = 0; j < D::kNIn; ++j) {
     nm.lo_x[j] = decode_key(hmm[j]);
-    nm.hi_x[j] = decode_key(hmm[kNIn + j]);
+    nm.hi_x[j] = decode_key(hmm[D::kNIn + j]);
   }
   if ((rc = upload_norm(s, st))) return rc;
+  const Norm<NS>* dnorm = static_cast<const Norm<NS>*>(s->norm);
   // epochs of shuffled mini-batches (full batches only)
   std::vector<int> order(static_cast<size_t>(n));
   for (int64_t i = 0; i < n; ++i) order[i] = static_cast<int>(i);
@@ -982,17 +1038,18 @@ int chem_surrogate_train(chem_ctx* ctx, const float* X, const float* Yt, int64_t
     cudaMemcpyAsync(s->idx, order.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st);
     cudaMemsetAsync(s->loss, 0, sizeof(float), st);
     for (int64_t bi = 0; bi < nb; ++bi, ++step) {
-      batch_kernel<<<(B + 127) / 128, 128, 0, st>>>(X, Yt, s->idx + bi * B, B, s->norm, s->Xn, s->Tn, s->Raw);
-      if ((rc = forward(s, B, st))) return fail_cuda(static_cast<cudaError_t>(rc), "forward");
-      if ((rc = backward(s, B, cfg->err_weight, st))) return fail_cuda(static_cast<cudaError_t>(rc), "backward");
+      batch_kernel<NS><<<(B + 127) / 128, 128, 0, st>>>(X, Yt, s->idx + bi * B, B, dnorm, s->Xn, s->Tn, s->Raw);
+      if ((rc = forward<NS>(s, B, st))) return fail_cuda(static_cast<cudaError_t>(rc), "forward");
+      if ((rc = backward<NS>(s, B, cfg->err_weight, st))) return fail_cuda(static_cast<cudaError_t>(rc), "backward");
+      // cosine decay of the learning rate from cfg->lr (step 0) towards 0 (step total_steps)
       const double lr = 0.5 * cfg->lr * (1.0 + std::cos(3.14159265358979 * static_cast<double>(step) /
                                                           static_cast<double>(total_steps)));
       ++s->adam_t;
       const float c1 = static_cast<float>(1.0 - std::pow(0.9, static_cast<double>(s->adam_t)));
       const float c2 = static_cast<float>(1.0 - std::pow(0.999, static_cast<double>(s->adam_t)));
-      adamw_kernel<<<(kNParams + 255) / 256, 256, 0, st>>>(s->params, s->grads, s->m, s->v, kNParams,
-                                                           static_cast<float>(lr), 0.9f, 0.999f, 1e-8f,
-                                                           static_cast<float>(cfg->weight_decay), c1, c2);
+      adamw_kernel<<<(D::kNParams + 255) / 256, 256, 0, st>>>(s->params, s->grads, s->m, s->v, D::kNParams,
+                                                              static_cast<float>(lr), 0.9f, 0.999f, 1e-8f,
+                                                              static_cast<float>(cfg->weight_decay), c1, c2);
     }
     float l = 0.0f;
     cudaMemcpyAsync(&l, s->loss, sizeof(float), cudaMemcpyDeviceToHost, st);
@@ -1003,47 +1060,91 @@ int chem_surrogate_train(chem_ctx* ctx, const float* X, const float* Yt, int64_t
   return device_status(s, st);
 }
 
+template <int NS>
+int surrogate_grads_t(State* s, const float* X, const float* Yt, int32_t n, float err_weight, float* grads,
+                      float* loss, cudaStream_t st) {
+  int rc = ensure_batch<NS>(s, n);
+  if (rc) return rc;
+  cudaMemsetAsync(s->loss, 0, sizeof(float), st);
+  batch_kernel<NS><<<(n + 127) / 128, 128, 0, st>>>(X, Yt, nullptr, n, static_cast<const Norm<NS>*>(s->norm), s->Xn,
+                                                    s->Tn, s->Raw);
+  if ((rc = forward<NS>(s, n, st))) return fail_cuda(static_cast<cudaError_t>(rc), "forward");
+  if ((rc = backward<NS>(s, n, err_weight, st))) return fail_cuda(static_cast<cudaError_t>(rc), "backward");
+  cudaMemcpyAsync(grads, s->grads, sizeof(float) * Dims<NS>::kNParams, cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(loss, s->loss, sizeof(float), cudaMemcpyDeviceToDevice, st);
+  return device_status(s, st);
+}
+
+template <int NS>
+int surrogate_forward_t(State* s, const float* X, int32_t n, float* out, cudaStream_t st) {
+  using D = Dims<NS>;
+  constexpr int Bmax = 8192;
+  int rc = ensure_batch<NS>(s, n < Bmax ? (n + 127) / 128 * 128 : Bmax);
+  if (rc) return rc;
+  for (int b0 = 0; b0 < n; b0 += Bmax) {
+    const int B = n - b0 < Bmax ? n - b0 : Bmax;
+    batch_kernel<NS><<<(B + 127) / 128, 128, 0, st>>>(X + static_cast<int64_t>(b0) * D::kNIn, nullptr, nullptr, B,
+                                                      static_cast<const Norm<NS>*>(s->norm), s->Xn, nullptr, nullptr);
+    if ((rc = forward<NS>(s, B, st))) return fail_cuda(static_cast<cudaError_t>(rc), "forward");
+    cudaMemcpyAsync(out + static_cast<int64_t>(b0) * D::kNOut, s->Z[4], sizeof(float) * B * D::kNOut,
+                    cudaMemcpyDeviceToDevice, st);
+  }
+  return device_status(s, st);
+}
+
+int launch_infer_ns(chem_ctx* ctx, State* s, const GatedArgs& g, cudaStream_t st) {
+  return SG_DISPATCH(s->ns, launch_infer, ctx, s, g, st);
+}
+
+}  // namespace
+
+extern "C" {
+
+int chem_surrogate_nparams(int32_t ns) {
+  if (ns == 9) return Dims<9>::kNParams;
+  if (ns == 53) return Dims<53>::kNParams;
+  return CHEM_EUNSUPPORTED;
+}
+
+int chem_surrogate_init(chem_ctx* ctx, uint64_t seed) {
+  if (!ctx) return CHEM_EINVAL;
+  const int ns = context_ns(ctx);
+  if (!surrogate_ns(ns)) return CHEM_EUNSUPPORTED;
+  return SG_DISPATCH(ns, surrogate_init_t, ctx, seed);
+}
+
+int chem_surrogate_train(chem_ctx* ctx, const float* X, const float* Yt, int64_t n, const chem_train_cfg* cfg,
+                         float* loss_per_epoch, void* stream) {
+  State* s = get_state(ctx);
+  if (!s || !X || !Yt || !cfg || cfg->epochs < 0 || cfg->batch < 128 || (cfg->batch % 128) || !(cfg->lr > 0) ||
+      n < cfg->batch || n > 0x7fffffffLL || !(cfg->weight_decay >= 0) || !(cfg->err_weight >= 0))
+    return CHEM_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  return SG_DISPATCH(s->ns, surrogate_train_t, s, X, Yt, n, cfg, loss_per_epoch, st);
+}
+
 int chem_surrogate_grads(chem_ctx* ctx, const float* X, const float* Yt, int32_t n, float err_weight, float* grads,
                          float* loss, void* stream) {
   State* s = get_state(ctx);
   if (!s || !X || !Yt || n < 128 || (n % 128) || !grads || !loss || !(err_weight >= 0)) return CHEM_EINVAL;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  int rc = ensure_batch(s, n);
-  if (rc) return rc;
-  cudaMemsetAsync(s->loss, 0, sizeof(float), st);
-  batch_kernel<<<(n + 127) / 128, 128, 0, st>>>(X, Yt, nullptr, n, s->norm, s->Xn, s->Tn, s->Raw);
-  if ((rc = forward(s, n, st))) return fail_cuda(static_cast<cudaError_t>(rc), "forward");
-  if ((rc = backward(s, n, err_weight, st))) return fail_cuda(static_cast<cudaError_t>(rc), "backward");
-  cudaMemcpyAsync(grads, s->grads, sizeof(float) * kNParams, cudaMemcpyDeviceToDevice, st);
-  cudaMemcpyAsync(loss, s->loss, sizeof(float), cudaMemcpyDeviceToDevice, st);
-  return device_status(s, st);
+  return SG_DISPATCH(s->ns, surrogate_grads_t, s, X, Yt, n, err_weight, grads, loss, st);
 }
 
 int chem_surrogate_forward(chem_ctx* ctx, const float* X, int32_t n, float* out, void* stream) {
   State* s = get_state(ctx);
   if (!s || !X || n < 1 || !out) return CHEM_EINVAL;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  constexpr int Bmax = 8192;
-  int rc = ensure_batch(s, n < Bmax ? (n + 127) / 128 * 128 : Bmax);
-  if (rc) return rc;
-  for (int b0 = 0; b0 < n; b0 += Bmax) {
-    const int B = n - b0 < Bmax ? n - b0 : Bmax;
-    batch_kernel<<<(B + 127) / 128, 128, 0, st>>>(X + static_cast<int64_t>(b0) * kNIn, nullptr, nullptr, B, s->norm,
-                                                  s->Xn, nullptr, nullptr);
-    if ((rc = forward(s, B, st))) return fail_cuda(static_cast<cudaError_t>(rc), "forward");
-    cudaMemcpyAsync(out + static_cast<int64_t>(b0) * kNOut, s->Z[4], sizeof(float) * B * kNOut,
-                    cudaMemcpyDeviceToDevice, st);
-  }
-  return device_status(s, st);
+  return SG_DISPATCH(s->ns, surrogate_forward_t, s, X, n, out, st);
 }
 
 int chem_surrogate_params(chem_ctx* ctx, float* dst, const float* src, void* stream) {
   State* s = get_state(ctx);
   if (!s || (!dst && !src)) return CHEM_EINVAL;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (dst) cudaMemcpyAsync(dst, s->params, sizeof(float) * kNParams, cudaMemcpyDefault, st);
+  if (dst) cudaMemcpyAsync(dst, s->params, sizeof(float) * s->nparams, cudaMemcpyDefault, st);
   if (src) {
-    cudaMemcpyAsync(s->params, src, sizeof(float) * kNParams, cudaMemcpyDefault, st);
+    cudaMemcpyAsync(s->params, src, sizeof(float) * s->nparams, cudaMemcpyDefault, st);
     s->blob_dirty = true;
   }
   return fail_cuda(cudaStreamSynchronize(st), "params");
@@ -1052,35 +1153,40 @@ int chem_surrogate_params(chem_ctx* ctx, float* dst, const float* src, void* str
 int chem_surrogate_save(chem_ctx* ctx, void* buf, size_t cap, size_t* size) {
   State* s = get_state(ctx);
   if (!s || !size) return CHEM_EINVAL;
-  const size_t need = 16 + sizeof(Norm) + sizeof(float) * kNParams;
+  const size_t need = 16 + s->hnorm.size() + sizeof(float) * s->nparams;
   *size = need;
   if (!buf) return CHEM_OK;
   if (cap < need) return CHEM_EINVAL;
   unsigned char* b = static_cast<unsigned char*>(buf);
-  const int32_t hdr[4] = {0x47534843 /* "CHSG" */, 1, kNS, kNParams};
+  const int32_t hdr[4] = {0x47534843 /* "CHSG" */, 1, s->ns, s->nparams};
   std::memcpy(b, hdr, 16);
-  std::memcpy(b + 16, &s->hnorm, sizeof(Norm));
-  return fail_cuda(cudaMemcpy(b + 16 + sizeof(Norm), s->params, sizeof(float) * kNParams, cudaMemcpyDeviceToHost),
+  std::memcpy(b + 16, s->hnorm.data(), s->hnorm.size());
+  return fail_cuda(cudaMemcpy(b + 16 + s->hnorm.size(), s->params, sizeof(float) * s->nparams, cudaMemcpyDeviceToHost),
                    "save");
 }
 
 int chem_surrogate_load(chem_ctx* ctx, const void* buf, size_t size) {
-  if (!ctx || !buf) return CHEM_EINVAL;
-  const size_t need = 16 + sizeof(Norm) + sizeof(float) * kNParams;
+  if (!ctx || !buf || size < 16) return CHEM_EINVAL;
+  const int ns = context_ns(ctx);
+  if (!surrogate_ns(ns)) return CHEM_EUNSUPPORTED;
+  const int nparams = chem_surrogate_nparams(ns);
+  const size_t norm_bytes = ns == 9 ? sizeof(Norm<9>) : sizeof(Norm<53>);
+  const size_t need = 16 + norm_bytes + sizeof(float) * nparams;
   if (size != need) return CHEM_EINVAL;
   const unsigned char* b = static_cast<const unsigned char*>(buf);
   int32_t hdr[4];
   std::memcpy(hdr, b, 16);
-  if (hdr[0] != 0x47534843 || hdr[1] != 1 || hdr[2] != kNS || hdr[3] != kNParams) return CHEM_EINVAL;
+  if (hdr[0] != 0x47534843 || hdr[1] != 1 || hdr[2] != ns || hdr[3] != nparams) return CHEM_EINVAL;
   int rc = CHEM_OK;
   if (!get_state(ctx) && (rc = chem_surrogate_init(ctx, 0))) return rc;
   State* s = get_state(ctx);
-  Norm nm;
-  std::memcpy(&nm, b + 16, sizeof(Norm));
-  if (nm.ncons != s->hnorm.ncons) return CHEM_EINVAL;   // saved for another mechanism
-  s->hnorm = nm;
-  rc = fail_cuda(cudaMemcpy(s->params, b + 16 + sizeof(Norm), sizeof(float) * kNParams, cudaMemcpyHostToDevice),
-                 "load");
+  int ncons_saved = 0, ncons_now = 0;
+  const size_t ncons_off = norm_bytes - 4 * sizeof(int);   // Norm ends with ncons, pad[3]
+  std::memcpy(&ncons_saved, b + 16 + ncons_off, sizeof(int));
+  std::memcpy(&ncons_now, s->hnorm.data() + ncons_off, sizeof(int));
+  if (ncons_saved != ncons_now) return CHEM_EINVAL;   // saved for another mechanism
+  std::memcpy(s->hnorm.data(), b + 16, norm_bytes);
+  rc = fail_cuda(cudaMemcpy(s->params, b + 16 + norm_bytes, sizeof(float) * nparams, cudaMemcpyHostToDevice), "load");
   return rc ? rc : upload_norm(s, nullptr);
 }
 
@@ -1109,7 +1215,7 @@ int chem_advance_gated(chem_ctx* ctx, float* T, float* p, float* Y, int64_t ld, 
     g.atol = 1e-10f;
     g.accepted = accepted;
     g.substeps = substeps;
-    if ((rc = launch_infer(ctx, s, g, st))) return rc;
+    if ((rc = launch_infer_ns(ctx, s, g, st))) return rc;
   }
   // every cell the gate rejected goes through the plain bulk / stiff path
   if ((rc = ctx_advance_skip(ctx, T, p, Y, ld, rho, e, n, dt, substeps, accepted, st))) return rc;
@@ -1139,7 +1245,7 @@ int chem_surrogate_infer(chem_ctx* ctx, const float* T, const float* Y, int64_t 
   g.gate_log10 = -INFINITY;
   g.atol = 1e-10f;
   g.out = out;
-  const int rc = launch_infer(ctx, s, g, st);
+  const int rc = launch_infer_ns(ctx, s, g, st);
   return rc ? rc : device_status(s, st);
 }
 

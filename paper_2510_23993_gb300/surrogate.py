@@ -20,7 +20,7 @@ def make_pairs(ctx, T, p, Y, dt_box, rtol=1e-6, atol=1e-11, fp64_rates=True, rho
     from (T, p, Y) by chem_state_from_TpY when not given.  rtol and atol are the integrator's
     tolerances for the pairs (tighter than the 1e-4 / 1e-10 the pairs are judged by); fp64_rates
     evaluates the stiff cells' rates in FP64 (CHEM_FLAG_FP64_RATES), which the 1e-10 bar on
-    near-equilibrium minor species needs.  Returns (X [m][12], Yt [m][10], keep [n] bool) with
+    near-equilibrium minor species needs.  Returns (X [m][ns + 3], Yt [m][ns + 1], keep [n] bool) with
     X rows (T, p, dt, Y) and Yt rows (Y1, T1) for the m cells the integrator finished.  The
     context's box table is replaced and its parameters are restored afterwards."""
     n, nbox = T.shape[0], len(dt_box)

@@ -16,3 +16,9 @@ def pytest_configure(config):
 def h2mech():
     import synth
     return synth.h2_air_mechanism(0)
+
+
+@pytest.fixture(scope="session")
+def hcmech():
+    import synth
+    return synth.hydrocarbon_mechanism(0)

@@ -26,11 +26,6 @@ def _built():
     chem.build()
 
 
-@pytest.fixture(scope="module")
-def hcmech():
-    return synth.hydrocarbon_mechanism(0)
-
-
 def _dev(*arrs):
     return [torch.from_numpy(np.ascontiguousarray(a)).to(DEV) for a in arrs]
 

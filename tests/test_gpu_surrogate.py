@@ -1,15 +1,22 @@
-"""The learned surrogate on the GPU: gradients, statistics, fused inference, the gate, the gain.
+"""The learned surrogate on the GPU: gradients, optimiser, statistics, fused inference, the gate.
+
+Both compiled shapes are covered: the 9-species mechanism (12 inputs -> 11 outputs) and the
+53-species mechanism (56 -> 55).
 
 * The loss gradient of the tensor-core training path equals the FP64 oracle's reverse-mode
-  gradient (oracle/mlp.py, pinned by finite differences): tightly when the oracle rounds the
-  operands of its products to BF16 as the interface states, loosely in plain FP64.
-* The normalisation statistics and the conserved directions the library derives match the
-  oracle's (the directions from the element matrix, the library's from the reaction span).
+  gradient (oracle/mlp.py, pinned by finite differences) entry by entry: within 3e-3 of the
+  layer's rms (plus a floor of 1e-6 of the layer's largest entry) against the oracle that rounds
+  the operands of its products to BF16 as the interface states, and within 0.1 of the rms
+  against plain FP64 (where BF16 rounding of the operands is the difference).
+* A few full-batch training steps (AdamW, cosine-annealed learning rate, decoupled weight decay)
+  give the parameters the oracle's optimiser gives from the same start, entry by entry.
+* The normalisation statistics and the conserved directions the library derives (Gram-Schmidt
+  on the reaction span) match the oracle's (null space by SVD), and contain the element masses.
 * The fused inference kernel equals the GEMM forward and the oracle's forward.
 * With a gate that accepts nothing the gated step is bit-identical to chem_advance.
-* A network trained on pairs from the plain integrator (a sample of them checked against the
-  oracle) accepts cells whose oracle error is within the parity bar (false-accept rate
-  measured), and the gain over the plain method is measured on a reacting-sheet field.
+* A network trained on pairs from the plain integrator (4,096 of them checked against the
+  oracle) accepts cells whose oracle error is within the parity bar: the false-accept rate is
+  measured on >= 1e5 held-out cells of a reacting sheet, separately for cold and reacting cells.
 """
 import time
 
@@ -36,6 +43,11 @@ def _built():
     chem.build()
 
 
+@pytest.fixture(params=[9, 53], ids=["ns9", "ns53"])
+def mech(request, h2mech, hcmech):
+    return h2mech if request.param == 9 else hcmech
+
+
 def _raw_batch(mech, n, seed, premix_frac=0.5):
     """Raw rows X = (T, p, dt, Y) and Yt = (Y1, T1) (synthetic new states), float32."""
     T, p, Y, dt = synth.surrogate_samples(mech, n, seed=seed, premix_frac=premix_frac)
@@ -50,18 +62,19 @@ def _raw_batch(mech, n, seed, premix_frac=0.5):
 def _oracle_checkpoint(mech, X, Yt, seed):
     """Normalisation from the data (oracle), conserved directions from the element matrix, seeded
     He-initialised parameters; returns the checkpoint bytes and the stored (FP32) values."""
+    ns = mech["ns"]
     Xd, Yd = X.astype(np.float64), Yt.astype(np.float64)
     F = mlp.features(Xd[:, 0], Xd[:, 1], Xd[:, 2], Xd[:, 3:])
-    A = mlp.targets(Xd[:, 0], Xd[:, 3:], Yd[:, :9], Yd[:, 9])
+    A = mlp.targets(Xd[:, 0], Xd[:, 3:], Yd[:, :ns], Yd[:, ns])
     norm = mlp.norm_from_data(F, A)
-    C = mlp.conserved_basis(mech["elem"], mech["W"])
-    norm["C"] = np.vstack([C, np.zeros((mlp.MAX_CONS - C.shape[0], 9))])
+    C = mlp.conserved_directions(mech["W"], mech["nu_f"], mech["nu_r"])
+    norm["C"] = np.vstack([C, np.zeros((mlp.MAX_CONS - C.shape[0], ns))])
     norm["ncons"] = C.shape[0]
     rng = np.random.default_rng(seed)
+    w = mlp.widths(ns)
     layers = []
     for l in range(5):
-        nin, nout = mlp.WIDTHS[l], mlp.WIDTHS[l + 1]
-        layers.append((rng.normal(0, np.sqrt(2.0 / nin), (nout, nin)), rng.normal(0, 0.05, nout)))
+        layers.append((rng.normal(0, np.sqrt(2.0 / w[l]), (w[l + 1], w[l])), rng.normal(0, 0.05, w[l + 1])))
     params = mlp.flatten(layers).astype(np.float32)
     blob = mlp.pack_checkpoint(norm, params)
     return blob, mlp.unpack_checkpoint(blob)
@@ -71,10 +84,11 @@ def _dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
 
 
-def _layer_slices():
+def _layer_slices(ns):
     out, off = [], 0
+    w = mlp.widths(ns)
     for l in range(5):
-        nin, nout = mlp.WIDTHS[l], mlp.WIDTHS[l + 1]
+        nin, nout = w[l], w[l + 1]
         out.append((f"W{l + 1}", slice(off, off + nin * nout)))
         off += nin * nout
         out.append((f"b{l + 1}", slice(off, off + nout)))
@@ -82,14 +96,15 @@ def _layer_slices():
     return out
 
 
-def test_gradients_match_oracle(h2mech):
-    X, Yt = _raw_batch(h2mech, 1024, seed=11)
-    blob, (norm, params) = _oracle_checkpoint(h2mech, X, Yt, seed=3)
-    ctx = chem.Context(h2mech, max_cells=1024)
+def test_gradients_match_oracle_entry_by_entry(mech):
+    ns = mech["ns"]
+    X, Yt = _raw_batch(mech, 1024, seed=11)
+    blob, (norm, params) = _oracle_checkpoint(mech, X, Yt, seed=3)
+    ctx = chem.Context(mech, max_cells=1024)
     ctx.surrogate_init(0)
     ctx.surrogate_load(blob)
-    n = mlp.n_params()
-    assert chem.chem_surrogate_nparams() == n
+    n = mlp.n_params(ns)
+    assert chem.chem_surrogate_nparams(ns) == n
     g = torch.zeros(n, dtype=torch.float32, device=DEV)
     loss = torch.zeros(1, dtype=torch.float32, device=DEV)
     ctx.surrogate_grads(_dev(X), _dev(Yt), 0.1, g, loss)
@@ -99,29 +114,79 @@ def test_gradients_match_oracle(h2mech):
     l_ex, g_ex = mlp.surrogate_loss_and_grad(norm, params, Xd, Yd, 0.1, bf16_products=False)
     assert abs(loss.item() - l_emu) <= 1e-4 * l_emu
     assert abs(loss.item() - l_ex) <= 2e-2 * l_ex
-    for name, sl in _layer_slices():
-        e_emu = np.linalg.norm(g[sl] - g_emu[sl]) / np.linalg.norm(g_emu[sl])
-        e_ex = np.linalg.norm(g[sl] - g_ex[sl]) / np.linalg.norm(g_ex[sl])
-        assert e_emu <= 3e-3, (name, e_emu)
-        assert e_ex <= 5e-2, (name, e_ex)
+    worst = {}
+    for name, sl in _layer_slices(ns):
+        rms = np.sqrt(np.mean(g_emu[sl] ** 2))
+        floor = 1e-6 * np.max(np.abs(g_emu[sl]))
+        d_emu = np.abs(g[sl] - g_emu[sl])
+        d_ex = np.abs(g[sl] - g_ex[sl])
+        worst[name] = (float(np.max(d_emu) / rms), float(np.max(d_ex) / rms))
+        bad = d_emu > 3e-3 * rms + floor
+        assert not bad.any(), (name, int(bad.sum()), worst[name])
+        assert np.all(d_ex <= 0.1 * rms + floor), (name, worst[name])
+    print(f"\nns={ns}: worst |g - g_oracle| / layer rms (BF16-emulating, FP64): {worst}")
     ctx.close()
 
 
-def test_statistics_and_conserved_directions_match_oracle(h2mech):
-    X, Yt = _raw_batch(h2mech, 8192, seed=12)
-    ctx = chem.Context(h2mech, max_cells=16)
+def test_training_steps_match_oracle_optimiser(mech):
+    """E full-batch steps of chem_surrogate_train (each epoch is one step: batch = n) against the
+    oracle's AdamW with the cosine schedule from the same start.  The first step of Adam moves
+    every parameter by about lr sign(g), so a parameter whose gradient is tiny is sensitive to
+    the sign of that gradient; entries whose first-step oracle gradient is at least 0.1 of the
+    layer's rms must agree to 5e-3 lr per step, every entry to 2 lr per step."""
+    ns = mech["ns"]
+    n, E, lr, wd = 1024, 4, 1e-3, 1e-2
+    X, Yt = _raw_batch(mech, n, seed=31)
+    blob, (norm0, p0) = _oracle_checkpoint(mech, X, Yt, seed=7)
+    ctx = chem.Context(mech, max_cells=n)
+    ctx.surrogate_init(0)          # zero moments, step count 0
+    ctx.surrogate_load(blob)       # the start parameters
+    losses = ctx.surrogate_train(_dev(X), _dev(Yt), epochs=E, batch=n, lr=lr, weight_decay=wd, err_weight=0.1,
+                                 seed=5)
+    assert len(losses) == E and all(np.isfinite(losses))
+    norm, _ = mlp.unpack_checkpoint(ctx.surrogate_save())   # the statistics the GPU trained with
+    pg = torch.zeros(mlp.n_params(ns), dtype=torch.float32, device=DEV)
+    assert chem.chem_surrogate_params(ctx.handle, dst=pg) == chem.CHEM_OK
+    p_gpu = pg.cpu().numpy()
+    Xd, Yd = X.astype(np.float64), Yt.astype(np.float64)
+    w, m, v = p0.copy(), np.zeros_like(p0), np.zeros_like(p0)
+    g1 = None
+    for s in range(E):
+        _, g = mlp.surrogate_loss_and_grad(norm, w, Xd, Yd, 0.1, bf16_products=True)
+        g1 = g if g1 is None else g1
+        w, m, v = mlp.adamw_step(w, g, m, v, s + 1, mlp.cosine_lr(lr, s, E), wd)
+    d = np.abs(p_gpu.astype(np.float64) - w)
+    steady = np.zeros(d.size, bool)
+    for _, sl in _layer_slices(ns):
+        steady[sl] = np.abs(g1[sl]) >= 0.1 * np.sqrt(np.mean(g1[sl] ** 2))
+    moved = np.abs(w - p0)
+    print(f"\nns={ns}: parameters moved up to {moved.max():.2e}; |GPU - oracle| max {d.max():.2e}, over entries "
+          f"with a steady gradient ({steady.mean():.2f} of them) {d[steady].max():.2e}; losses {losses}")
+    assert np.all(d[steady] <= 5e-3 * lr * E)
+    assert np.all(d <= 2 * lr * E)
+    assert np.median(d) <= 1e-3 * lr * E
+    ctx.close()
+
+
+def test_statistics_and_conserved_directions_match_oracle(mech):
+    ns = mech["ns"]
+    X, Yt = _raw_batch(mech, 8192, seed=12)
+    ctx = chem.Context(mech, max_cells=16)
     ctx.surrogate_init(0)
     norm0, _ = mlp.unpack_checkpoint(ctx.surrogate_save())
     C_lib = norm0["C"][:norm0["ncons"]]
-    C_or = mlp.conserved_basis(h2mech["elem"], h2mech["W"])
+    C_or = mlp.conserved_directions(mech["W"], mech["nu_f"], mech["nu_r"])
     assert norm0["ncons"] == C_or.shape[0]
     assert np.allclose(C_lib.T @ C_lib, C_or.T @ C_or, atol=1e-6)
+    # the element masses are among them
+    E = mlp.conserved_basis(mech["elem"], mech["W"])
+    assert np.allclose(E @ (C_lib.T @ C_lib), E, atol=1e-6)
     losses = ctx.surrogate_train(_dev(X), _dev(Yt), epochs=0)
     assert losses == []
     norm, _ = mlp.unpack_checkpoint(ctx.surrogate_save())
     Xd, Yd = X.astype(np.float64), Yt.astype(np.float64)
     F = mlp.features(Xd[:, 0], Xd[:, 1], Xd[:, 2], Xd[:, 3:])
-    A = mlp.targets(Xd[:, 0], Xd[:, 3:], Yd[:, :9], Yd[:, 9])
+    A = mlp.targets(Xd[:, 0], Xd[:, 3:], Yd[:, :ns], Yd[:, ns])
     ref = mlp.norm_from_data(F, A)
     assert np.all(np.abs(norm["mu_x"] - ref["mu_x"]) <= 1e-4 * ref["sd_x"])
     assert np.allclose(norm["sd_x"], ref["sd_x"], rtol=1e-4)
@@ -133,20 +198,21 @@ def test_statistics_and_conserved_directions_match_oracle(h2mech):
     ctx.close()
 
 
-def test_fused_inference_matches_gemm_and_oracle(h2mech):
+def test_fused_inference_matches_gemm_and_oracle(mech):
+    ns = mech["ns"]
     n = 1000   # 7 full tiles of 128 cells and a ragged tail
-    T, p, Y, _ = synth.surrogate_samples(h2mech, n, seed=13, premix_frac=0.5)
+    T, p, Y, _ = synth.surrogate_samples(mech, n, seed=13, premix_frac=0.5)
     dt = 3e-8
     T32, p32, Y32 = T.astype(np.float32), p.astype(np.float32), np.ascontiguousarray(Y, dtype=np.float32)
-    rho, e = oracle.state_from_TpY(h2mech, T32, p32, Y32)
+    rho, e = oracle.state_from_TpY(mech, T32, p32, Y32)
     X = np.column_stack([T32, p32, np.full(n, dt, np.float32), Y32.T]).astype(np.float32)
-    Xn, Ytn = _raw_batch(h2mech, 4096, seed=14)
-    blob, (norm, params) = _oracle_checkpoint(h2mech, Xn, Ytn, seed=4)
-    ctx = chem.Context(h2mech, max_cells=n)
+    Xn, Ytn = _raw_batch(mech, 4096, seed=14)
+    blob, (norm, params) = _oracle_checkpoint(mech, Xn, Ytn, seed=4)
+    ctx = chem.Context(mech, max_cells=n)
     ctx.surrogate_load(blob)   # creates the surrogate on first use
-    o_fused = torch.zeros((n, 11), dtype=torch.float32, device=DEV)
+    o_fused = torch.zeros((n, ns + 2), dtype=torch.float32, device=DEV)
     ctx.surrogate_infer(_dev(T32), _dev(Y32), _dev(rho.astype(np.float32)), _dev(e.astype(np.float32)), dt, o_fused)
-    o_gemm = torch.zeros((n, 11), dtype=torch.float32, device=DEV)
+    o_gemm = torch.zeros((n, ns + 2), dtype=torch.float32, device=DEV)
     ctx.surrogate_forward(_dev(X), o_gemm)
     o_fused, o_gemm = o_fused.cpu().numpy().astype(np.float64), o_gemm.cpu().numpy().astype(np.float64)
     o_emu = mlp.surrogate_outputs(norm, params, X.astype(np.float64), bf16_products=True)
@@ -168,19 +234,19 @@ def test_fused_inference_matches_gemm_and_oracle(h2mech):
     ctx.close()
 
 
-def _sheet(mech, n_edge, seed):
-    T, p, Y, hot = synth.sheet_field(mech, n=n_edge, seed=seed)
+def _sheet(mech, n_edge, seed, frac=0.05):
+    T, p, Y, hot = synth.sheet_field(mech, n=n_edge, seed=seed, frac=frac)
     T, p, Y = T.astype(np.float32), p.astype(np.float32), np.ascontiguousarray(Y, dtype=np.float32)
     rho, e = oracle.state_from_TpY(mech, T, p, Y)
     return T, p, Y, rho.astype(np.float32), e.astype(np.float32), hot
 
 
-def test_gate_closed_equals_plain(h2mech):
-    X, Yt = _raw_batch(h2mech, 4096, seed=15)
-    blob, _ = _oracle_checkpoint(h2mech, X, Yt, seed=5)
-    T, p, Y, rho, e, _ = _sheet(h2mech, 24, seed=3)
+def test_gate_closed_equals_plain(mech):
+    X, Yt = _raw_batch(mech, 4096, seed=15)
+    blob, _ = _oracle_checkpoint(mech, X, Yt, seed=5)
+    T, p, Y, rho, e, _ = _sheet(mech, 24 if mech["ns"] == 9 else 12, seed=3)
     n = T.size
-    ctx = chem.Context(h2mech, max_cells=n)
+    ctx = chem.Context(mech, max_cells=n)
     ctx.surrogate_load(blob)
     a = [_dev(v) for v in (T, p, Y)]
     sub_a = torch.zeros(n, dtype=torch.int32, device=DEV)
@@ -197,27 +263,47 @@ def test_gate_closed_equals_plain(h2mech):
     ctx.close()
 
 
-def _errors(mech, rho, e, T0, Y0, dt, T, Y):
+def _oracle_advance(mech, rho, e, T0, Y0, dt):
+    """oracle.advance with a scalar dt or one dt per cell (cells grouped by their dt)."""
+    if np.ndim(dt) == 0:
+        return oracle.advance(mech, rho, e, T0, Y0, float(dt))
+    T = np.empty(T0.shape[0])
+    Y = np.empty(Y0.shape)
+    for d in np.unique(dt):
+        m = dt == d
+        T[m], _, Y[:, m], _ = oracle.advance(mech, rho[m], e[m], T0[m], Y0[:, m], float(d))
+    return T, None, Y, None
+
+
+def _errors(mech, rho, e, T0, Y0, dt, T, Y, conditioning=True):
     """Per-cell parity check against the oracle, with the conditioning allowance of the plain
-    FP32 path (3x the oracle's response to a one-ulp change of e); returns (bad, eT, eY_rel)."""
-    T_ref, _, Y_ref, _ = oracle.advance(mech, rho, e, T0, Y0, dt)
-    T_p, _, Y_p, _ = oracle.advance(mech, rho, e.astype(np.float64) * (1 + 2.0 ** -23), T0, Y0, dt)
+    FP32 path (3x the oracle's response to a one-ulp change of e, computed for the cells over the
+    strict bar only); returns (bad, eT, eY_rel)."""
+    T_ref, _, Y_ref, _ = _oracle_advance(mech, rho, e, T0, Y0, dt)
     big = Y_ref >= Y_BIG
-    cT = np.abs(T_p - T_ref) / T_ref
-    cY = np.where(big, np.abs(Y_p - Y_ref) / np.maximum(Y_ref, 1e-300), np.abs(Y_p - Y_ref))
     eT = np.abs(T.astype(np.float64) - T_ref) / T_ref
     eY = np.where(big, np.abs(Y.astype(np.float64) - Y_ref) / np.maximum(Y_ref, 1e-300),
                   np.abs(Y.astype(np.float64) - Y_ref))
-    bad = (eT > TOL_T + 3 * cT) | np.any(eY > np.where(big, TOL_Y, ABS_Y) + 3 * cY, axis=0)
+    bad = (eT > TOL_T) | np.any(eY > np.where(big, TOL_Y, ABS_Y), axis=0)
+    if conditioning and bad.any():
+        i = np.nonzero(bad)[0]
+        dt_i = dt[i] if np.ndim(dt) else dt
+        T_p, _, Y_p, _ = _oracle_advance(mech, rho[i], e[i].astype(np.float64) * (1 + 2.0 ** -23), T0[i],
+                                         Y0[:, i], dt_i)
+        cT = np.abs(T_p - T_ref[i]) / T_ref[i]
+        cY = np.where(big[:, i], np.abs(Y_p - Y_ref[:, i]) / np.maximum(Y_ref[:, i], 1e-300), np.abs(Y_p - Y_ref[:, i]))
+        bad[i] = (eT[i] > TOL_T + 3 * cT) | np.any(eY[:, i] > np.where(big[:, i], TOL_Y, ABS_Y) + 3 * cY, axis=0)
     return bad, eT, np.where(big, eY, 0.0).max(0)
 
 
 def test_trained_gate_accuracy_and_gain(h2mech):
-    """Train on 262,144 integrator-made pairs, then one gated step of a 64^3 reacting sheet."""
+    """Train on 262,144 integrator-made pairs (4,096 of them checked against the oracle), then one
+    gated step of a 48^3 reacting sheet (110,592 held-out cells): every accepted cell against the
+    oracle, the false-accept rate reported for cold and reacting cells separately."""
     nbox, m = 256, 1024
     n_train = nbox * m
     Ts, ps, Ys, dts = synth.surrogate_samples(h2mech, n_train, seed=21, premix_frac=0.5)
-    ctx = chem.Context(h2mech, max_cells=max(n_train, 64 ** 3))
+    ctx = chem.Context(h2mech, max_cells=max(n_train, 48 ** 3))
     Td, pd, Yd = _dev(Ts.astype(np.float32)), _dev(ps.astype(np.float32)), _dev(Ys.astype(np.float32))
     t0 = time.perf_counter()
     X, Yt, keep = surrogate.make_pairs(ctx, Td, pd, Yd, dts[:nbox])
@@ -227,27 +313,25 @@ def test_trained_gate_accuracy_and_gain(h2mech):
     kept = keep.float().mean().item()
     print(f"\npairs: {t_pairs:.1f} s, kept {kept:.4f}, status {st_pairs}")
     assert kept > 0.95
-    # a sample of the training pairs against the oracle
+    # 4,096 of the training pairs against the oracle (the pairs' own dt each)
     rng = np.random.default_rng(0)
-    idx = rng.choice(X.shape[0], 24, replace=False)
+    idx = rng.choice(X.shape[0], 4096, replace=False)
     Xs, Ys_ = X[idx].cpu().numpy().astype(np.float64), Yt[idx].cpu().numpy().astype(np.float64)
-    fails = []
-    for r in range(len(idx)):
-        T0, p0, dt, Y0 = Xs[r, 0], Xs[r, 1], Xs[r, 2], Xs[r, 3:]
-        rho, e = oracle.state_from_TpY(h2mech, np.float32([T0]), np.float32([p0]), Y0.astype(np.float32)[:, None])
-        rho, e = rho.astype(np.float32), e.astype(np.float32)
-        bad, eT, eY = _errors(h2mech, rho, e, np.array([T0]), Y0[:, None], dt, np.array([Ys_[r, 9]]),
-                              Ys_[r, :9][:, None])
-        if bad.any():
-            fails.append((r, T0, p0, dt, float(eT[0]), float(eY[0])))
-    assert not fails, fails
+    T0, p0, dt0, Y0 = Xs[:, 0], Xs[:, 1], Xs[:, 2], np.ascontiguousarray(Xs[:, 3:].T)
+    rho0, e0 = oracle.state_from_TpY(h2mech, T0.astype(np.float32), p0.astype(np.float32), Y0.astype(np.float32))
+    rho0, e0 = rho0.astype(np.float32), e0.astype(np.float32)
+    t0 = time.perf_counter()
+    bad, eT, eY = _errors(h2mech, rho0, e0, T0, Y0, dt0, Ys_[:, 9], np.ascontiguousarray(Ys_[:, :9].T))
+    print(f"training pairs vs oracle: {int(bad.sum())}/4096 over the bar, max rel err T {eT.max():.2e} "
+          f"Y {eY.max():.2e} ({time.perf_counter() - t0:.1f} s)")
+    assert not bad.any()
     ctx.surrogate_init(1)
     t0 = time.perf_counter()
     losses = ctx.surrogate_train(X, Yt, epochs=40, batch=4096, lr=1e-3, err_weight=0.1, seed=1)
     t_train = time.perf_counter() - t0
     assert losses[-1] < 0.2 * losses[0], losses
-    # one gated step of a reacting sheet against the plain step
-    T, p, Y, rho, e, hot = _sheet(h2mech, 64, seed=5)
+    # one gated step of a held-out reacting sheet against the plain step
+    T, p, Y, rho, e, hot = _sheet(h2mech, 48, seed=5)
     n = T.size
     dt = 1e-8
     rho_d, e_d = _dev(rho), _dev(e)
@@ -267,55 +351,58 @@ def test_trained_gate_accuracy_and_gain(h2mech):
         res[mode] = dict(ms=1e3 * (time.perf_counter() - t0), st=ctx.status(), T=s[0].cpu().numpy(),
                          Y=s[2].cpu().numpy(), acc=acc.cpu().numpy().astype(bool), na=na)
     g, pl = res["gated"], res["plain"]
-    # diagnostics: the error head over the field, and the true error of the prediction there
-    o = torch.zeros((n, 11), dtype=torch.float32, device=DEV)
-    ctx.surrogate_infer(_dev(T), _dev(Y), rho_d, e_d, dt, o)
-    o = o.cpu().numpy()
-    hd = np.percentile(o[:, 10], [1, 10, 50, 90])
-    print(f"\nerror head over the field: p1/p10/p50/p90 {hd}; cold {np.percentile(o[~hot, 10], [1, 50, 99])}, "
-          f"hot {np.percentile(o[hot, 10], [1, 50, 99])}")
     assert g["na"] == int(g["acc"].sum()) and g["na"] > 0
     assert g["st"]["nqueued"] <= pl["st"]["nqueued"]
-    # accepted cells against the oracle: the false-accept rate on a sample (hot cells first)
+    # every accepted cell against the oracle
     acc_idx = np.nonzero(g["acc"])[0]
-    hot_acc = acc_idx[hot[acc_idx]]
-    pick = np.concatenate([hot_acc[:100], rng.choice(acc_idx, min(200, acc_idx.size), replace=False)])
-    bad, eT, eY = _errors(h2mech, rho[pick], e[pick], T[pick], Y[:, pick], dt, g["T"][pick], g["Y"][:, pick])
-    far = bad.mean()
+    t0 = time.perf_counter()
+    bad, eT, eY = _errors(h2mech, rho[acc_idx], e[acc_idx], T[acc_idx], Y[:, acc_idx], dt, g["T"][acc_idx],
+                          g["Y"][:, acc_idx])
+    hot_acc = hot[acc_idx]
+    n_cold, n_hot = int((~hot_acc).sum()), int(hot_acc.sum())
+    fa_cold = int(bad[~hot_acc].sum())
+    fa_hot = int(bad[hot_acc].sum())
     print(f"\nsurrogate: pairs {t_pairs:.1f} s, train {t_train:.1f} s, loss {losses[0]:.3g} -> {losses[-1]:.3g}; "
-          f"accepted {g['na']}/{n} ({g['na'] / n:.3f}; hot accepted {hot_acc.size}/{int(hot.sum())}); "
-          f"false-accept {bad.sum()}/{pick.size}; max rel err T {eT.max():.2e} Y {eY.max():.2e}; "
-          f"queued plain {pl['st']['nqueued']} gated {g['st']['nqueued']}; "
-          f"ms plain {pl['ms']:.2f} gated {g['ms']:.2f}")
-    assert far <= 0.02
+          f"held-out cells {n}: accepted {g['na']} ({g['na'] / n:.3f}); false accepts: cold {fa_cold}/{n_cold}, "
+          f"reacting {fa_hot}/{n_hot} (of {int(hot.sum())} reacting); max rel err T {eT.max():.2e} Y {eY.max():.2e} "
+          f"(oracle {time.perf_counter() - t0:.1f} s); queued plain {pl['st']['nqueued']} gated "
+          f"{g['st']['nqueued']}; ms plain {pl['ms']:.2f} gated {g['ms']:.2f}")
+    assert n >= 100_000 and n_cold >= 100_000
+    assert fa_cold == 0
+    assert fa_hot <= max(0.02 * n_hot, 0)
     # rejected cells took the plain path: identical to the plain step there
     rej = ~g["acc"]
     assert np.array_equal(g["T"][rej], pl["T"][rej]) and np.array_equal(g["Y"][:, rej], pl["Y"][:, rej])
     ctx.close()
 
 
-def test_save_load_round_trip_and_gated_edge_cases(h2mech):
+def test_save_load_round_trip_and_gated_edge_cases(mech):
     """A saved surrogate reloads bit for bit into another context; the gated step handles an
     empty call, a padded leading dimension and invalid cells (never accepted, flagged by the
     plain path)."""
-    X, Yt = _raw_batch(h2mech, 4096, seed=16)
-    blob, _ = _oracle_checkpoint(h2mech, X, Yt, seed=6)
-    T, p, Y, rho, e, hot = _sheet(h2mech, 10, seed=6)
+    ns = mech["ns"]
+    X, Yt = _raw_batch(mech, 4096, seed=16)
+    blob, _ = _oracle_checkpoint(mech, X, Yt, seed=6)
+    T, p, Y, rho, e, hot = _sheet(mech, 10, seed=6, frac=0.1)
     n = T.size
-    a = chem.Context(h2mech, max_cells=n)
+    a = chem.Context(mech, max_cells=n)
     a.surrogate_load(blob)
     saved = a.surrogate_save()
     assert saved == blob
-    b = chem.Context(h2mech, max_cells=n)
+    b = chem.Context(mech, max_cells=n)
     b.surrogate_load(saved)
-    oa = torch.zeros((n, 11), dtype=torch.float32, device=DEV)
+    oa = torch.zeros((n, ns + 2), dtype=torch.float32, device=DEV)
     ob = torch.zeros_like(oa)
     a.surrogate_infer(_dev(T), _dev(Y), _dev(rho), _dev(e), 1e-8, oa)
     b.surrogate_infer(_dev(T), _dev(Y), _dev(rho), _dev(e), 1e-8, ob)
     assert torch.equal(oa, ob)
+    # a checkpoint of the other shape is refused
+    other = chem.Context(synth.hydrocarbon_mechanism(0) if ns == 9 else synth.h2_air_mechanism(0), max_cells=16)
+    assert chem.chem_surrogate_load(other.handle, saved) == chem.CHEM_EINVAL
+    other.close()
     # empty call
     z = torch.zeros(0, dtype=torch.float32, device=DEV)
-    zY = torch.zeros((9, 0), dtype=torch.float32, device=DEV)
+    zY = torch.zeros((ns, 0), dtype=torch.float32, device=DEV)
     assert a.advance_gated(z, z, zY, z, z, 1e-8, 1e-5, torch.zeros(0, dtype=torch.uint8, device=DEV),
                            torch.zeros(0, dtype=torch.int32, device=DEV)) == 0
     # padded leading dimension and two invalid cells, against the same step with ld = n
@@ -323,7 +410,7 @@ def test_save_load_round_trip_and_gated_edge_cases(h2mech):
     Tb, Yb = T.copy(), Y.copy()
     Tb[3] = np.nan
     Yb[0, 7] = -0.5
-    tY = torch.full((9, ld), -3.0, dtype=torch.float32, device=DEV)
+    tY = torch.full((ns, ld), -3.0, dtype=torch.float32, device=DEV)
     tY[:, :n] = torch.from_numpy(Yb).to(DEV)
     acc = torch.zeros(n, dtype=torch.uint8, device=DEV)
     sub = torch.zeros(n, dtype=torch.int32, device=DEV)

@@ -8,7 +8,13 @@
   physical clamps;
 * the conservative correction: feasible, a minimiser of the weighted norm, the identity on
   feasible changes, and element-conserving for the mechanism's element matrix;
-* the state error vanishes for an exact prediction.
+* the state error vanishes for an exact prediction;
+* the optimiser (AdamW with a cosine-annealed learning rate) against closed forms: a constant
+  gradient gives steps of exactly lr sign(g) (the bias corrections cancel the moments' zero
+  start), a zero gradient shrinks the weights by prod (1 - lr_s wd) (the decay is decoupled from
+  the adaptive step), a rescaled gradient gives the same steps, and the schedule starts at lr,
+  passes lr / 2 half-way, is antisymmetric about it and sums to lr (S + 1) / 2 over S steps;
+* everything also at the 53-species shape (56 inputs, 55 outputs).
 """
 import numpy as np
 import pytest
@@ -46,18 +52,25 @@ def test_gradient_matches_finite_differences_small_net():
     x = rng.normal(size=(16, 12))
     t = rng.normal(size=(16, 10))
     e_star = rng.normal(size=16)
-    _fd_check(layers, x, t, e_star, 0.3, range(mlp.n_params(widths)))
+    _fd_check(layers, x, t, e_star, 0.3, range(sum(widths[l + 1] * (widths[l] + 1) for l in range(3))))
 
 
-def test_gradient_matches_finite_differences_full_width():
+@pytest.mark.parametrize("ns", [9, 53])
+def test_gradient_matches_finite_differences_full_width(ns):
     rng = np.random.default_rng(1)
-    layers = _small_layers(rng, mlp.WIDTHS)
-    x = rng.normal(size=(8, mlp.N_IN))
-    t = rng.normal(size=(8, mlp.N_TGT))
+    w = mlp.widths(ns)
+    layers = _small_layers(rng, w)
+    x = rng.normal(size=(8, ns + 3))
+    t = rng.normal(size=(8, ns + 1))
     e_star = rng.normal(size=8)
-    n = mlp.n_params()
-    picks = list(rng.choice(n, 40, replace=False)) + [0, n - 1, n - 12]   # first W1, last bias, error-head row
+    n = mlp.n_params(ns)
+    picks = list(rng.choice(n, 40, replace=False)) + [0, n - 1, n - ns - 3]   # first W1, last bias, error-head row
     _fd_check(layers, x, t, e_star, 0.5, picks)
+
+
+def test_parameter_counts():
+    assert mlp.n_params(9) == 52619 and mlp.n_params(53) == 63927
+    assert mlp.ns_of_params(52619) == 9 and mlp.ns_of_params(63927) == 53
 
 
 def test_gelu_is_x_times_normal_cdf():
@@ -139,6 +152,22 @@ def test_conservative_correction(h2mech):
     assert np.allclose(mlp.conserve(C, Y0, feas), feas, rtol=1e-12, atol=1e-20)
 
 
+def test_conserved_directions_of_both_mechanisms(h2mech, hcmech):
+    """The complement of the reaction span: orthonormal, orthogonal to every reaction vector, of
+    dimension ns - rank, and containing the element-mass directions.  The 53-species mechanism has
+    one direction more than it has elements: its N2 takes part in no reaction while other
+    N-bearing species do."""
+    for mech, n_extra in ((h2mech, 0), (hcmech, 1)):
+        C = mlp.conserved_directions(mech["W"], mech["nu_f"], mech["nu_r"])
+        R = mech["W"][:, None] * (mech["nu_r"] - mech["nu_f"]).astype(float).T
+        assert np.allclose(C @ C.T, np.eye(C.shape[0]), atol=1e-12)
+        assert np.allclose(C @ R, 0.0, atol=1e-12)
+        assert C.shape[0] == mech["ns"] - np.linalg.matrix_rank(R)
+        E = mlp.conserved_basis(mech["elem"], mech["W"])
+        assert np.allclose(E @ C.T @ C, E, atol=1e-12)
+        assert C.shape[0] == E.shape[0] + n_extra <= mlp.MAX_CONS
+
+
 def test_state_error_vanishes_for_exact_prediction(h2mech):
     rng = np.random.default_rng(6)
     n = 200
@@ -160,15 +189,85 @@ def test_state_error_vanishes_for_exact_prediction(h2mech):
     assert np.all(mlp.state_error(norm, o2, Y0, T0, Y1, T1) > 1e-12)
 
 
-def test_checkpoint_round_trip():
+@pytest.mark.parametrize("ns", [9, 53])
+def test_checkpoint_round_trip(ns):
     rng = np.random.default_rng(7)
-    norm = dict(mu_x=rng.normal(size=12), sd_x=rng.uniform(1, 2, 12), mu_y=rng.normal(size=10),
-                sd_y=rng.uniform(1, 2, 10), lo_x=rng.normal(size=12), hi_x=rng.normal(size=12),
-                C=rng.normal(size=(4, 9)), ncons=3)
-    params = rng.normal(size=mlp.n_params()).astype(np.float32)
+    ni, nt = ns + 3, ns + 1
+    norm = dict(mu_x=rng.normal(size=ni), sd_x=rng.uniform(1, 2, ni), mu_y=rng.normal(size=nt),
+                sd_y=rng.uniform(1, 2, nt), lo_x=rng.normal(size=ni), hi_x=rng.normal(size=ni),
+                C=rng.normal(size=(mlp.MAX_CONS, ns)), ncons=3)
+    params = rng.normal(size=mlp.n_params(ns)).astype(np.float32)
     blob = mlp.pack_checkpoint(norm, params)
     n2, p2 = mlp.unpack_checkpoint(blob)
     assert n2["ncons"] == 3 and np.array_equal(p2, params.astype(np.float64))
     for k in ("mu_x", "sd_y", "lo_x", "hi_x"):
         assert np.array_equal(n2[k], np.asarray(norm[k], np.float32).astype(np.float64))
-    assert len(blob) == 16 + 4 * (12 * 4 + 10 * 2 + 36 + 4) + 4 * mlp.n_params()
+    assert np.array_equal(n2["C"], np.asarray(norm["C"], np.float32).astype(np.float64))
+    assert len(blob) == 16 + 4 * (ni * 4 + nt * 2 + mlp.MAX_CONS * ns + 4) + 4 * mlp.n_params(ns)
+
+
+def test_adamw_constant_gradient_steps_are_lr_sign_g():
+    """With the same gradient every step, the bias-corrected moments equal g and g^2 exactly, so
+    (without decay) every step is lr g / (|g| + eps): the running averages' zero start is undone."""
+    rng = np.random.default_rng(8)
+    w0 = rng.normal(size=1000)
+    g = rng.normal(size=1000) * 10.0 ** rng.uniform(-3, 3, 1000)
+    w, m, v = w0.copy(), np.zeros(1000), np.zeros(1000)
+    lr = 1e-3
+    for t in range(1, 26):
+        w, m, v = mlp.adamw_step(w, g, m, v, t, lr, 0.0)
+    expect = w0 - 25 * lr * g / (np.abs(g) + 1e-8)
+    assert np.allclose(w, expect, rtol=0, atol=1e-12)
+
+
+def test_adamw_zero_gradient_decays_independently_of_the_moments():
+    """Decoupled weight decay: with g = 0 the adaptive term vanishes and the weights shrink by
+    (1 - lr_s wd) per step, whatever the second-moment estimate (the coupled L2 form would divide
+    the decay by sqrt(v))."""
+    rng = np.random.default_rng(9)
+    w0 = rng.normal(size=100)
+    lr, wd, S = 2e-3, 0.1, 40
+    w, m, v = w0.copy(), np.zeros(100), np.full(100, 1e-6)
+    shrink = 1.0
+    for s in range(S):
+        lr_s = mlp.cosine_lr(lr, s, S)
+        w, m, v = mlp.adamw_step(w, np.zeros(100), m, v, s + 1, lr_s, wd)
+        shrink *= 1.0 - lr_s * wd
+    assert np.allclose(w, w0 * shrink, rtol=1e-14, atol=0)
+
+
+def test_adamw_is_invariant_to_gradient_scale():
+    rng = np.random.default_rng(10)
+    w0 = rng.normal(size=500)
+    gs = [rng.normal(size=500) * 10.0 ** rng.uniform(-2, 2, 500) for _ in range(12)]
+    out = []
+    for c in (1.0, 1e3):
+        w, m, v = w0.copy(), np.zeros(500), np.zeros(500)
+        for t, g in enumerate(gs, start=1):
+            w, m, v = mlp.adamw_step(w, c * g, m, v, t, 1e-3, 1e-4, eps=1e-30)
+        out.append(w)
+    assert np.allclose(out[0], out[1], rtol=0, atol=1e-12)
+
+
+def test_cosine_schedule_closed_forms():
+    lr, S = 1e-3, 1000
+    lrs = np.array([mlp.cosine_lr(lr, s, S) for s in range(S)])
+    assert lrs[0] == lr and abs(lrs[S // 2] - lr / 2) < 1e-18
+    assert np.all(np.diff(lrs) < 0) and lrs[-1] > 0
+    # antisymmetric about lr / 2: lr_s + lr_{S - s} = lr
+    assert np.allclose(lrs[1:] + lrs[1:][::-1], lr, rtol=0, atol=1e-18)
+    # sum_{s < S} cos(pi s / S) = 1, so the schedule sums to lr (S + 1) / 2
+    assert abs(lrs.sum() - lr * (S + 1) / 2) < 1e-15
+
+
+def test_adamw_minimises_a_quadratic():
+    """AdamW with the cosine schedule drives a separable quadratic to its minimiser (w* = 0 with
+    zero decay; with decay the minimiser of the decayed objective lies between)."""
+    rng = np.random.default_rng(11)
+    target = rng.normal(size=50)
+    w, m, v = np.zeros(50), np.zeros(50), np.zeros(50)
+    S = 4000
+    for s in range(S):
+        g = w - target
+        w, m, v = mlp.adamw_step(w, g, m, v, s + 1, mlp.cosine_lr(0.05, s, S), 0.0)
+    assert np.max(np.abs(w - target)) < 1e-3
