@@ -271,6 +271,22 @@ int chem_temperature(chem_ctx *ctx, const float *Y, int64_t ld, const float *e, 
 int chem_rates(chem_ctx *ctx, const float *rho, const float *T, const float *Y, int64_t ld,
                int64_t n, float *dYdt, void *stream);
 
+/* chem_rates for the 53-species mechanisms with the stoichiometric contractions of the matrix
+ * form (Sec. 3.2; App. C weighs library GEMMs against a hand-written product) on the tensor
+ * cores: per tile of 128 cells, ln C . nu_f^T, ln C . nu_r^T and C . eff^T (third-body
+ * concentrations) are BF16 tensor-core products accumulated in FP32, the rates of progress are
+ * formed per cell and reaction in FP32 on the CUDA cores, and q . dnu is a fourth tensor-core
+ * product.  Each FP32 operand enters as three BF16 parts (x = b0 + b1 + b2, 24 significant bits),
+ * so the result has the precision of chem_rates (FP32); a cell with a rate of progress above
+ * 1e37 in magnitude (or not finite) is redone with FP64 rates of progress.  Same arguments, layout and
+ * output as chem_rates (device pointers, Y and dYdt [ns][ld], asynchronous on `stream`).
+ * CHEM_EUNSUPPORTED for a context whose mechanism is not a 53-species one with at most 32
+ * third-body reactions (the operand image, ~140 KB, is built by chem_init).  A tensor-core
+ * completion that does not arrive within the spin limit sets the status that chem_status
+ * reports as CHEM_ECUDA. */
+int chem_rates_tc(chem_ctx *ctx, const float *rho, const float *T, const float *Y, int64_t ld,
+                  int64_t n, float *dYdt, void *stream);
+
 /* chem_advance for callers that cannot allocate device memory (no counterpart in the paper).
  * Real-time loops that may not block on the allocator, plugins that may only use the buffers
  * handed to them, or processes with a capped allocator cannot call chem_init, which allocates.

@@ -115,6 +115,7 @@ def lib():
         L.chem_state_from_TpY_f64.argtypes = [vp, vp, vp, vp, i64, i64, vp, vp, vp]
         L.chem_temperature.argtypes = [vp, vp, i64, vp, i64, vp, vp]
         L.chem_rates.argtypes = [vp, vp, vp, vp, i64, i64, vp, vp]
+        L.chem_rates_tc.argtypes = [vp, vp, vp, vp, i64, i64, vp, vp]
         L.chem_status.argtypes = [vp, vp, _P(chem_stats)]
         L.chem_advance_noalloc.argtypes = [_P(chem_mechanism), _P(chem_params), vp, vp, vp, i64, vp, vp, i64, d,
                                            vp, _P(chem_stats), vp]
@@ -150,7 +151,7 @@ def lib():
         L.chem_strerror.restype = ctypes.c_char_p
         for name in ("chem_init", "chem_set_params", "chem_advance", "chem_advance_f64", "chem_advance_host",
                      "chem_advance_explicit", "chem_state_from_TpY", "chem_state_from_TpY_f64", "chem_temperature", "chem_rates",
-                     "chem_status"):
+                     "chem_rates_tc", "chem_status"):
             getattr(L, name).restype = i32
         _lib = L
     return _lib
@@ -350,6 +351,10 @@ def chem_rates(ctx, rho, T, Y, ld, n, dYdt, stream=None):
     return lib().chem_rates(ctx, _dp(rho), _dp(T), _dp(Y), int(ld), int(n), _dp(dYdt), _stream(stream))
 
 
+def chem_rates_tc(ctx, rho, T, Y, ld, n, dYdt, stream=None):
+    return lib().chem_rates_tc(ctx, _dp(rho), _dp(T), _dp(Y), int(ld), int(n), _dp(dYdt), _stream(stream))
+
+
 def chem_status(ctx, stream=None):
     s = chem_stats()
     _check(lib().chem_status(ctx, _stream(stream), ctypes.byref(s)), "chem_status")
@@ -462,6 +467,11 @@ class Context:
     def rates(self, rho, T, Y, dYdt, stream=None):
         n = self._check_state(T, Y, rho, dYdt)
         _check(chem_rates(self.handle, rho, T, Y, Y.stride(0), n, dYdt, stream), "chem_rates")
+
+    def rates_tc(self, rho, T, Y, dYdt, stream=None):
+        """chem_rates with the stoichiometric contractions on the tensor cores (53 species)."""
+        n = self._check_state(T, Y, rho, dYdt)
+        _check(chem_rates_tc(self.handle, rho, T, Y, Y.stride(0), n, dYdt, stream), "chem_rates_tc")
 
     def status(self, stream=None):
         return chem_status(self.handle, stream).as_dict()

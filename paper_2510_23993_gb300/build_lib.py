@@ -12,7 +12,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libchem.so")
-SOURCES = ["abi.cu", "bulk.cu", "stiff.cu", "noalloc.cu", "pack.cu", "peak.cu", "tune.cu", "mlp.cu", "surrogate.cu", "large.cu", "explicit.cu", "multikernel.cu", "layout.cu"]
+SOURCES = ["abi.cu", "bulk.cu", "stiff.cu", "noalloc.cu", "pack.cu", "peak.cu", "tune.cu", "mlp.cu", "surrogate.cu", "large.cu", "explicit.cu", "multikernel.cu", "layout.cu", "rates_tc.cu"]
 HEADERS = ["chem_device.cuh", "internal.h", "tc.cuh", "kernel_abi.cuh", "stiff_body.cuh"]
 NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -58,6 +58,8 @@ struct chem_ctx {
   long long cont_cap = 0;
   // chem_advance_explicit: FP64 time, temperature and mass fractions of each cell (first use)
   double* xcell = nullptr;
+  // chem_rates_tc: the tensor-core operand image of a large mechanism (rates_tc.cu)
+  unsigned char* tc_img = nullptr;
 };
 
 namespace {
@@ -317,6 +319,12 @@ int chem_init(const chem_mechanism* mech, const chem_params* params, int64_t max
   for (auto& e : c->ev)
     if (cudaEventCreate(&e) != cudaSuccess) return fail(CHEM_ECUDA);
   if ((rc = ensure_two_pass(c))) return fail(rc);
+  if (large && rates_tc_supported(c->ns, c->ntb)) {
+    const std::vector<unsigned char> img = rates_tc_image(mech, blob.data());
+    if (cudaMalloc(&c->tc_img, img.size()) != cudaSuccess) return fail(CHEM_ENOMEM);
+    if ((rc = cuda_fail(cudaMemcpy(c->tc_img, img.data(), img.size(), cudaMemcpyHostToDevice), "copy operands")))
+      return fail(rc);
+  }
   *out = c;
   return CHEM_OK;
 }
@@ -354,6 +362,7 @@ void chem_destroy(chem_ctx* ctx) {
   cudaFree(ctx->cont_key);
   cudaFree(ctx->cont_sorted);
   cudaFree(ctx->xcell);
+  cudaFree(ctx->tc_img);
   delete ctx;
 }
 
@@ -639,6 +648,16 @@ int chem_rates(chem_ctx* ctx, const float* rho, const float* T, const float* Y, 
                            : launch_rates(ctx->ns, ctx->blob, ctx->blob_bytes, rho, T, Y, ld, n, dYdt,
                                           &ctx->ws->status, static_cast<cudaStream_t>(stream));
   return r == -1 ? CHEM_EUNSUPPORTED : cuda_fail(static_cast<cudaError_t>(r), "rates kernel");
+}
+
+int chem_rates_tc(chem_ctx* ctx, const float* rho, const float* T, const float* Y, int64_t ld, int64_t n,
+                  float* dYdt, void* stream) {
+  if (!ctx || n < 0 || (n > 0 && (!rho || !T || !Y || !dYdt || ld < n))) return CHEM_EINVAL;
+  if (!ctx->tc_img) return CHEM_EUNSUPPORTED;
+  if (n == 0) return CHEM_OK;
+  const int r = launch_rates_tc(ctx->ns, ctx->nr, ctx->ntb, ctx->tc_img, ctx->blob, rho, T, Y, ld, n, dYdt, &ctx->ws->status,
+                                static_cast<cudaStream_t>(stream));
+  return r == -1 ? CHEM_EUNSUPPORTED : cuda_fail(static_cast<cudaError_t>(r), "tensor-core rates kernel");
 }
 
 int chem_status(chem_ctx* ctx, void* stream, chem_stats* out) {

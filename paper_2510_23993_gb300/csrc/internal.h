@@ -1,5 +1,6 @@
 // internal.h -- host/device contract between the C ABI (abi.cu) and the kernels.
 #pragma once
+#include <vector>
 #include <cstdint>
 
 #include <cuda_runtime.h>
@@ -48,6 +49,13 @@ int launch_rates_lg(int ns, int nr, int ntb, const unsigned char* blob, unsigned
                     const float* T, const float* Y, long long ld, long long n, float* dYdt, int* status,
                     cudaStream_t s);
 int occupancy_lg(int ns, int nr, int ntb, unsigned prefix, bool stiff, int* blocks_per_sm);
+
+// large mechanisms, rates with the stoichiometric contractions on the tensor cores (rates_tc.cu)
+bool rates_tc_supported(int ns, int ntb);
+std::vector<unsigned char> rates_tc_image(const chem_mechanism* m, const unsigned char* blob);
+int launch_rates_tc(int ns, int nr, int ntb, const unsigned char* img, const unsigned char* blob, const float* rho,
+                    const float* T, const float* Y, long long ld, long long n, float* dYdt, int* status,
+                    cudaStream_t s);
 
 int launch_state_from_TpY_f32(int ns, const unsigned char* blob, unsigned blob_bytes, const float* T,
                               const float* p, const float* Y, long long ld, long long n, float* rho,
