@@ -719,6 +719,33 @@ def run_study(args):
                                   "frac_of_measured_hbm": gbs / hbm if hbm else None}), flush=True)
             del X, p
         return
+    if args.study == "rates_tc":
+        # one size (--cells) of the 53-species rates: tensor-core kernel, warp-per-cell kernel and
+        # the cuBLAS sequence on the same inputs (inputs above L2 at the default size)
+        mech = synth.hydrocarbon_mechanism(0)
+        N = args.cells if args.cells != 16_000_000 else 1 << 20
+        rng = np.random.default_rng(0)
+        T = rng.uniform(800, 3000, N).astype(np.float32)
+        p = (rng.uniform(1, 20, N) * synth.P_ATM).astype(np.float32)
+        Y = np.ascontiguousarray(rng.dirichlet(np.full(mech["ns"], 0.3), size=N).T, dtype=np.float32)
+        ctx = chem.Context(mech, max_cells=N)
+        mk = chem.MultiKernelRates(mech, max_cells=N)
+        tT, tp, tY = (torch.from_numpy(a).to(dev) for a in (T, p, Y))
+        rho, e = torch.empty_like(tT), torch.empty_like(tT)
+        ctx.state_from_TpY(tT, tp, tY, rho, e)
+        f = torch.empty_like(tY)
+        t_c = _time_ms(lambda: ctx.rates_tc(rho, tT, tY, f), args.steps, torch)
+        t_f = _time_ms(lambda: ctx.rates(rho, tT, tY, f), args.steps, torch)
+        t_m = _time_ms(lambda: mk.rates(rho, tT, tY, f), args.steps, torch)
+        hbm = (2 * mech["ns"] + 2) * 4 * N      # Y read, dY/dt written, rho and T read
+        print(json.dumps({"study": "rates_tc", "mechanism": "53 species / 325 reactions", "cells": N,
+                          "tensor_core_ms": t_c, "fused_ms": t_f, "multikernel_ms": t_m,
+                          "tensor_core_cells_per_s": N / (t_c / 1e3), "fused_over_tensor_core": t_f / t_c,
+                          "multikernel_over_tensor_core": t_m / t_c,
+                          "tensor_core_hbm_GB_s": hbm / (t_c / 1e3) / 1e9}), flush=True)
+        mk.close()
+        ctx.close()
+        return
     if args.study == "rates":
         for name, mech in (("9 species / 21 reactions", synth.h2_air_mechanism(0)),
                            ("53 species / 325 reactions", synth.hydrocarbon_mechanism(0))):
@@ -840,7 +867,7 @@ def main():
     ap.add_argument("--paper-frac", type=float, default=0.05, help="relative change limit of the explicit scheme")
     ap.add_argument("--train-pairs", type=int, default=262144)
     ap.add_argument("--train-epochs", type=int, default=40)
-    ap.add_argument("--study", default=None, choices=["rates", "fusion", "layout"],
+    ap.add_argument("--study", default=None, choices=["rates", "rates_tc", "fusion", "layout"],
                     help="instead of the benchmark line: the comparisons with the paper's baseline strategies")
     args = ap.parse_args()
     if args.study:

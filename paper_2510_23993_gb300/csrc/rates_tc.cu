@@ -25,8 +25,11 @@
 //
 // Three groups of four warps share the tile: warps w, w + 4, w + 8 read the same 32 TMEM lanes
 // (cells) and take 16 of each chunk's 48 reactions, which triples the warps that hide the
-// latency of the per-reaction arithmetic.  The tensor-core operand images (~138 KB) are built
-// once per context and copied into each CTA's shared memory with one bulk async copy.
+// latency of the per-reaction arithmetic.  S is double-buffered in TMEM and issued two chunks
+// ahead, and the dnu product of a chunk completes while the next chunk's rates are computed, so
+// the CUDA cores wait on the tensor cores only at the start and the end of a tile.  The
+// tensor-core operand images (~138 KB) are built once per context and copied into each CTA's
+// shared memory with one bulk async copy.
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -51,8 +54,8 @@ static_assert(kChunk == 16 * kGroups, "one 16-column slice of each chunk per gro
 constexpr float kQFinite = 1.0e37f;
 // log-rate offset of the records' padding and irreversible reactions: exp() of it is 0
 constexpr float kLnOff = -2.0e4f;
-// TMEM columns of the accumulators
-constexpr uint32_t kColSf = 0, kColSr = 64, kColM = 128, kColW = 192, kTmemCols = 256;
+// TMEM columns of the accumulators: two S buffers (S_f at +0, S_r at +kSr), then M and w
+constexpr uint32_t kColS = 0, kSBuf = 128, kSr = 64, kColM = 256, kColW = 320, kTmemCols = 512;
 
 __host__ __device__ constexpr int nr_padded(int nr) { return (nr + kChunk - 1) / kChunk * kChunk; }
 
@@ -236,7 +239,9 @@ template <int NS>
 __global__ void __launch_bounds__(kThreads, 1) rates_tc_kernel(const RatesArgs a) {
   static_assert(NS <= kKS, "species exceed the padded K");
   extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ uint64_t bar_img, bar_mma;
+  // completion barriers of the tensor-core products: M, the two S buffers, dnu, and the final
+  // drain after a timeout
+  __shared__ uint64_t bar_img, bar_m, bar_s[2], bar_w, bar_f;
   __shared__ uint32_t s_taddr;
   __shared__ int s_bad[kTile];   // cells with a rate of progress beyond the FP32 range
   const ImgLayout L = img_layout(a.nr);
@@ -249,17 +254,33 @@ __global__ void __launch_bounds__(kThreads, 1) rates_tc_kernel(const RatesArgs a
   const int warp = threadIdx.x >> 5;
   const int grp = warp >> 2;                                   // reactions 16 grp .. 16 grp + 15 of each chunk
   const int row = (warp & 3) * 32 + (threadIdx.x & 31);        // the cell (TMEM lane) of this thread
+  const bool issuer = threadIdx.x == 0;
   if (warp == 0) tc::tmem_alloc(&s_taddr, kTmemCols);
-  if (threadIdx.x == 0) tc::mbar_init(&bar_mma, 1);
+  if (issuer) {
+    tc::mbar_init(&bar_m, 1);
+    tc::mbar_init(&bar_s[0], 1);
+    tc::mbar_init(&bar_s[1], 1);
+    tc::mbar_init(&bar_w, 1);
+    tc::mbar_init(&bar_f, 1);
+  }
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t taddr = s_taddr;
   const uint32_t lane_addr = taddr + (static_cast<uint32_t>((warp & 3) * 32) << 16);
   const int nchunk = L.nrp / kChunk;
-  const bool issuer = threadIdx.x == 0;
-  uint32_t phase = 0;
+  uint32_t pm = 0, ps0 = 0, ps1 = 0, pw = 0;   // phase parities of the barriers
   bool ok = true;
+  // S_f, S_r of chunk c into buffer b (issuer), completion on bar_s[b]
+  auto issue_s = [&](int c, int b) {
+    const unsigned off = static_cast<unsigned>(c) * kChunk * kKS * 2;   // rows of chunk c
+    const uint32_t col = kColS + b * kSBuf;
+    for (int s = 0; s < 3; ++s) {
+      mma_k(taddr + col, sX + s * kXBytes, kKS, sI + L.bf + off, kKS, kKS / 16, kChunk, s > 0);
+      mma_k(taddr + col + kSr, sX + s * kXBytes, kKS, sI + L.br + off, kKS, kKS / 16, kChunk, s > 0);
+    }
+    tc::mma_commit(&bar_s[b]);
+  };
   const long long ntiles = (a.n + kTile - 1) / kTile;
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const long long i = tile * kTile + row;
@@ -293,10 +314,10 @@ __global__ void __launch_bounds__(kThreads, 1) rates_tc_kernel(const RatesArgs a
       const int pa[6] = {0, 0, 1, 0, 2, 1}, pb[6] = {0, 1, 0, 2, 0, 1};   // the six largest split products
       for (int p = 0; p < 6; ++p)
         mma_k(taddr + kColM, sX + pa[p] * kXBytes, kKS, Be + pb[p] * kTB * kKS * 2, kKS, kKS / 16, kTB, p > 0);
-      tc::mma_commit(&bar_mma);
+      tc::mma_commit(&bar_m);
     }
-    ok = ok && tc::mbar_wait(&bar_mma, phase);
-    phase ^= 1u;
+    ok = ok && tc::mbar_wait(&bar_m, pm);
+    pm ^= 1u;
     if (!__syncthreads_and(ok)) { ok = false; break; }
     tc::fence_after_sync();
 #pragma unroll
@@ -317,11 +338,8 @@ __global__ void __launch_bounds__(kThreads, 1) rates_tc_kernel(const RatesArgs a
     __syncthreads();
     if (issuer) {
       tc::fence_after_sync();
-      for (int s = 0; s < 3; ++s) {
-        mma_k(taddr + kColSf, sX + s * kXBytes, kKS, sI + L.bf, kKS, kKS / 16, kChunk, s > 0);
-        mma_k(taddr + kColSr, sX + s * kXBytes, kKS, sI + L.br, kKS, kKS / 16, kChunk, s > 0);
-      }
-      tc::mma_commit(&bar_mma);
+      issue_s(0, 0);
+      if (nchunk > 1) issue_s(1, 1);
     }
     // per-cell basis of the log-rates
     const float lnT = __logf(T), invT = 1.0f / T, lnP0RT = m.lnP0R - lnT;
@@ -331,15 +349,22 @@ __global__ void __launch_bounds__(kThreads, 1) rates_tc_kernel(const RatesArgs a
     bool fine = true;
 #pragma unroll 1
     for (int c = 0; c < nchunk; ++c) {
-      ok = ok && tc::mbar_wait(&bar_mma, phase);   // S of chunk c (and the dnu product of chunk c - 1)
-      phase ^= 1u;
-      if (!__syncthreads_and(ok)) { ok = false; break; }
+      const int b = c & 1;
+      // S of chunk c (issued two chunks ahead)
+      if (b == 0) {
+        ok = ok && tc::mbar_wait(&bar_s[0], ps0);
+        ps0 ^= 1u;
+      } else {
+        ok = ok && tc::mbar_wait(&bar_s[1], ps1);
+        ps1 ^= 1u;
+      }
       tc::fence_after_sync();
       const int col = 16 * grp;
       const int r0 = c * kChunk + col;
+      const uint32_t scol = kColS + b * kSBuf + col;
       float sf[16], sr[16];
-      tc::tmem_ld16(lane_addr + kColSf + col, sf);
-      tc::tmem_ld16(lane_addr + kColSr + col, sr);
+      tc::tmem_ld16(lane_addr + scol, sf);
+      tc::tmem_ld16(lane_addr + scol + kSr, sr);
       float Mv[16];
 #pragma unroll
       for (int j = 0; j < 16; ++j) Mv[j] = 1.0f;
@@ -363,6 +388,10 @@ __global__ void __launch_bounds__(kThreads, 1) rates_tc_kernel(const RatesArgs a
         fine &= fabsf(qv) <= kQFinite;   // also false for inf and NaN
         q[j] = qv;
       }
+      if (c > 0) {   // the dnu product of chunk c - 1 has read Q
+        ok = ok && tc::mbar_wait(&bar_w, pw);
+        pw ^= 1u;
+      }
       float v8[8];
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
@@ -372,7 +401,7 @@ __global__ void __launch_bounds__(kThreads, 1) rates_tc_kernel(const RatesArgs a
       }
       tc::fence_async_smem();
       tc::fence_before_sync();
-      __syncthreads();
+      if (!__syncthreads_and(ok)) { ok = false; break; }
       if (issuer) {
         tc::fence_after_sync();
         const unsigned char* Bw = sI + L.bw + static_cast<unsigned>(c) * (kChunk / 8) * 128;   // K offset of chunk c
@@ -384,20 +413,14 @@ __global__ void __launch_bounds__(kThreads, 1) rates_tc_kernel(const RatesArgs a
             tc::mma_bf16(taddr + kColW, ad, bd, idesc, c > 0 || s > 0 || kk > 0);
           }
         }
-        if (c + 1 < nchunk) {
-          const unsigned off = static_cast<unsigned>(c + 1) * kChunk * kKS * 2;   // rows of chunk c + 1
-          for (int s = 0; s < 3; ++s) {
-            mma_k(taddr + kColSf, sX + s * kXBytes, kKS, sI + L.bf + off, kKS, kKS / 16, kChunk, s > 0);
-            mma_k(taddr + kColSr, sX + s * kXBytes, kKS, sI + L.br + off, kKS, kKS / 16, kChunk, s > 0);
-          }
-        }
-        tc::mma_commit(&bar_mma);
+        tc::mma_commit(&bar_w);
+        if (c + 2 < nchunk) issue_s(c + 2, b);   // buffer b has been read by every thread
       }
     }
     if (!ok) break;
     if (!fine) s_bad[row] = 1;
-    ok = ok && tc::mbar_wait(&bar_mma, phase);   // the last dnu product
-    phase ^= 1u;
+    ok = ok && tc::mbar_wait(&bar_w, pw);   // the last dnu product
+    pw ^= 1u;
     if (!__syncthreads_and(ok)) { ok = false; break; }
     tc::fence_after_sync();
     // ---- dY/dt = w W / rho: species columns 16 g (and 48 for group 0)
@@ -423,10 +446,13 @@ __global__ void __launch_bounds__(kThreads, 1) rates_tc_kernel(const RatesArgs a
     __syncthreads();   // TMEM columns, X, Q and s_bad are reused by the next tile
   }
   if (!ok) {
-    // a tensor-core completion did not arrive in time: record it and give it a second bounded
-    // chance to land before the accumulator is freed
-    if (threadIdx.x == 0) atomicOr(a.status, kFlagStage);
-    tc::mbar_wait(&bar_mma, phase ^ 1u);
+    // a tensor-core completion did not arrive in time: record it, then wait (bounded) for every
+    // product this CTA issued before the accumulator is freed
+    if (issuer) {
+      atomicOr(a.status, kFlagStage);
+      tc::mma_commit(&bar_f);
+    }
+    tc::mbar_wait(&bar_f, 0);
   }
   tc::fence_before_sync();
   __syncthreads();
