@@ -719,6 +719,41 @@ def run_study(args):
                                   "frac_of_measured_hbm": gbs / hbm if hbm else None}), flush=True)
             del X, p
         return
+    if args.study == "tail":
+        # the stiff phase's critical path: the distribution of substeps per stiff cell on the
+        # benchmark sheet, then the cells with the most substeps integrated alone (--tail-top
+        # sizes, 0 = none), so that the time of the longest cell can be set against the phase
+        mech = synth.h2_air_mechanism(0)
+        T, p, Y, hot = synth.sheet_field(mech, n=args.edge, seed=0)
+        T, p, Y = T.astype(np.float32), p.astype(np.float32), np.ascontiguousarray(Y, dtype=np.float32)
+        ctx = chem.Context(mech, max_cells=T.size)
+        tT, tp, tY = (torch.from_numpy(a).to(dev) for a in (T, p, Y))
+        trho, te = torch.empty_like(tT), torch.empty_like(tT)
+        ctx.state_from_TpY(tT, tp, tY, trho, te)
+        rho, e = trho.cpu().numpy(), te.cpu().numpy()
+
+        def run(idx, flags):
+            ctx.set_params(flags=chem.CHEM_FLAG_TIMING | flags)
+            d = [torch.from_numpy(np.ascontiguousarray(x)).to(dev) for x in (T[idx], p[idx], Y[:, idx], rho[idx], e[idx])]
+            sub = torch.zeros(len(idx), dtype=torch.int32, device=dev)
+            ctx.advance(d[0], d[1], d[2], d[3], d[4], 1e-8, sub)
+            return sub.cpu().numpy(), ctx.status()
+
+        order = chem.CHEM_FLAG_TWO_PASS | chem.CHEM_FLAG_ORDER_RATE
+        sub, st = run(np.arange(T.size), order)
+        q = sub[hot]
+        print(json.dumps({"study": "tail", "cells": int(T.size), "stiff_cells": int(st["nqueued"]),
+                          "stiff_ms": st["stiff_ms"], "substeps_pct_50_90_99_999": np.percentile(q, [50, 90, 99, 99.9]).tolist(),
+                          "substeps_max": int(q.max())}), flush=True)
+        top = np.argsort(-sub)
+        for k in [int(x) for x in args.tail_top.split(",") if int(x) > 0]:
+            idx = np.sort(top[:k])
+            s2, st2 = run(idx, order if k > 1 else 0)
+            print(json.dumps({"study": "tail_alone", "cells": k, "stiff_ms": st2["stiff_ms"],
+                              "substeps_max": int(s2.max()),
+                              "us_per_substep_of_longest": 1e3 * st2["stiff_ms"] / max(1, int(s2.max()))}), flush=True)
+        ctx.close()
+        return
     if args.study == "rates_tc":
         # one size (--cells) of the 53-species rates: tensor-core kernel, warp-per-cell kernel and
         # the cuBLAS sequence on the same inputs (inputs above L2 at the default size)
@@ -867,7 +902,8 @@ def main():
     ap.add_argument("--paper-frac", type=float, default=0.05, help="relative change limit of the explicit scheme")
     ap.add_argument("--train-pairs", type=int, default=262144)
     ap.add_argument("--train-epochs", type=int, default=40)
-    ap.add_argument("--study", default=None, choices=["rates", "rates_tc", "fusion", "layout"],
+    ap.add_argument("--tail-top", default="1,256,19456", help="--study tail: sizes of the longest-cell sets run alone")
+    ap.add_argument("--study", default=None, choices=["rates", "rates_tc", "tail", "fusion", "layout"],
                     help="instead of the benchmark line: the comparisons with the paper's baseline strategies")
     args = ap.parse_args()
     if args.study:
