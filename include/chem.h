@@ -326,12 +326,17 @@ typedef struct {
   float best_ms, default_ms;     /* timed advance with the chosen / the incoming settings */
   int32_t trials;                /* timed advances run */
   int32_t from_cache;            /* 1 if the choice came from the cache file */
+  int32_t stiff_block;           /* threads per CTA of the dense stiff kernel (64, 128, 256) */
+  int32_t quantum;               /* attempts per cell in the probe pass and in each continuation
+                                    round of the two-pass schedule (16, 32, 64) */
 } chem_tune_result;
 
 /* Autotuner of the launch configuration (the paper tuned K_max and the bulk-to-sparse threshold
  * by hand, Sec. 3.2 / App. D): times chem_advance on the caller's field (device arrays as for
- * chem_advance) for candidate values of k_bulk (1..3), the stiff-queue order and the resident
- * blocks per SM of both kernels (coordinate descent, best of two repetitions), applies the
+ * chem_advance) for candidate values of k_bulk (1..3), the stiff-queue order, the resident
+ * blocks per SM of both kernels and, for the dense (one cell per thread) stiff kernel, its CTA
+ * size and the two-pass scheduling quantum (coordinate descent, best of two repetitions; no
+ * candidate changes a cell's result), applies the
  * fastest to the context and returns it.  T, p, Y are restored to their input values on return
  * (the advanced state is discarded).  A set-up call: it allocates temporary device copies of T,
  * p, Y and synchronizes `stream`.  cache_path (may be NULL) names a text file: a matching entry

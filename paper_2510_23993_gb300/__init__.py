@@ -54,7 +54,8 @@ class chem_box(ctypes.Structure):
 class chem_tune_result(ctypes.Structure):
     _fields_ = [("k_bulk", ctypes.c_int32), ("flags", ctypes.c_int32), ("bulk_blocks_per_sm", ctypes.c_int32),
                 ("stiff_blocks_per_sm", ctypes.c_int32), ("best_ms", ctypes.c_float), ("default_ms", ctypes.c_float),
-                ("trials", ctypes.c_int32), ("from_cache", ctypes.c_int32)]
+                ("trials", ctypes.c_int32), ("from_cache", ctypes.c_int32), ("stiff_block", ctypes.c_int32),
+                ("quantum", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -33,6 +33,8 @@ struct chem_ctx {
   unsigned char* qkey = nullptr;   // device [max_cells], cost bucket of each queue entry
   int64_t last_n = 0;
   int bulk_grid = 0, stiff_grid = 0;
+  int stiff_block = kStiffBlock;                            // threads per CTA of the dense stiff kernel
+  int probe_att = kProbeAttempts, round_att = kRoundAttempts;   // two-pass scheduling quanta
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};   // CHEM_FLAG_TIMING
   // box table (chem_boxes_set)
   DevBox<float>* boxes = nullptr;
@@ -97,13 +99,15 @@ int ensure_two_pass(chem_ctx* c) {
 // The stiff phase: one persistent launch, or (two-pass mode) a probe launch, a counting sort of
 // the unfinished cells by remaining work, and a cooperative continuation launch: the sorted cells
 // run to completion from a shared queue until it is empty, then the cells still running are
-// parked and finished in rounds of kRoundAttempts steps, compacted into full warps between rounds.
+// parked and finished in rounds of round_att steps, compacted into full warps between rounds.
 template <typename S>
 int launch_stiff_phase(chem_ctx* c, AdvanceArgs<S> b, long long n, cudaStream_t st) {
   auto launch = [&](const AdvanceArgs<S>& x) {
-    if constexpr (sizeof(S) == 4) return launch_stiff_f32(c->ns, x, c->stiff_grid, st);
-    else return launch_stiff_f64(c->ns, x, c->stiff_grid, st);
+    if constexpr (sizeof(S) == 4) return launch_stiff_f32(c->ns, x, c->stiff_grid, c->stiff_block, st);
+    else return launch_stiff_f64(c->ns, x, c->stiff_grid, c->stiff_block, st);
   };
+  b.probe_att = c->probe_att;
+  b.round_att = c->round_att;
   b.pass = 0;
   b.cont_cap = 0;
   b.cont = nullptr;
@@ -221,6 +225,18 @@ void ctx_set_launch(chem_ctx* c, int bulk_grid, int stiff_grid) {
   c->stiff_grid = stiff_grid > 0 ? stiff_grid : 1;
 }
 void ctx_get_params(const chem_ctx* c, chem_params* p) { *p = c->prm; }
+// dense stiff kernel: threads per CTA and the two-pass scheduling quanta (large mechanisms: unused)
+void ctx_get_sched(const chem_ctx* c, int* stiff_block, int* probe_att, int* round_att, int* large) {
+  *stiff_block = c->stiff_block;
+  *probe_att = c->probe_att;
+  *round_att = c->round_att;
+  *large = c->large ? 1 : 0;
+}
+void ctx_set_sched(chem_ctx* c, int stiff_block, int probe_att, int round_att) {
+  if (stiff_block >= 32 && stiff_block <= kStiffBlockMax && stiff_block % 32 == 0) c->stiff_block = stiff_block;
+  if (probe_att >= 1) c->probe_att = probe_att;
+  if (round_att >= 1) c->round_att = round_att;
+}
 int occupancy_bulk(const chem_ctx* c) {
   int b = 0;
   const int r = c->large ? occupancy_lg(c->ns, c->nr, c->ntb, c->blob_bytes, false, &b)
@@ -230,7 +246,7 @@ int occupancy_bulk(const chem_ctx* c) {
 int occupancy_stiff(const chem_ctx* c) {
   int b = 0;
   const int r = c->large ? occupancy_lg(c->ns, c->nr, c->ntb, c->blob_bytes, true, &b)
-                         : stiff_occupancy(c->ns, c->blob_bytes, &b);
+                         : stiff_occupancy(c->ns, c->blob_bytes, c->stiff_block, &b);
   return (r != 0 || b < 1) ? 1 : b;
 }
 // surrogate state and the mechanism data it needs (surrogate.cu)

@@ -26,14 +26,14 @@ int pack_mechanism(const chem_mechanism* m, bool large, unsigned char* out, size
 // launchers (kernels.cu / stiff.cu); return cudaError_t as int, or -1 for unsupported ns
 int launch_bulk_f32(int ns, const AdvanceArgs<float>& a, int grid, cudaStream_t s);
 int launch_bulk_f64(int ns, const AdvanceArgs<double>& a, int grid, cudaStream_t s);
-int launch_stiff_f32(int ns, const AdvanceArgs<float>& a, int grid, cudaStream_t s);
-int launch_stiff_f64(int ns, const AdvanceArgs<double>& a, int grid, cudaStream_t s);
-size_t stiff_smem_bytes(int ns, unsigned blob_bytes, int nbox);
+int launch_stiff_f32(int ns, const AdvanceArgs<float>& a, int grid, int block, cudaStream_t s);
+int launch_stiff_f64(int ns, const AdvanceArgs<double>& a, int grid, int block, cudaStream_t s);
+size_t stiff_smem_bytes(int ns, unsigned blob_bytes, int nbox, int block);
 // counting sort of the queue by cost bucket, most expensive first: queue -> queue_out
 int launch_order_queue(Workspace* ws, const int* queue, const unsigned char* qkey, int* queue_out,
                        long long n, cudaStream_t s, bool continuations = false);
 size_t bulk_smem_bytes(unsigned blob_bytes, int nbox);
-int stiff_occupancy(int ns, unsigned blob_bytes, int* blocks_per_sm);
+int stiff_occupancy(int ns, unsigned blob_bytes, int block, int* blocks_per_sm);
 int bulk_occupancy(int ns, bool f64, unsigned blob_bytes, int* blocks_per_sm);
 
 // the paper's explicit integration loop (explicit.cu)

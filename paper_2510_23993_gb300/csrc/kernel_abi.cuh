@@ -35,6 +35,11 @@ struct DevBox {
   int level, pad;
 };
 
+// default scheduling quanta of the two-pass stiff integration (chem_tune may change them; the
+// results do not depend on them)
+constexpr int kProbeAttempts = 32;  // implicit steps per cell in the probe pass
+constexpr int kRoundAttempts = 32;  // implicit steps per cell and continuation round
+
 template <typename S>
 struct AdvanceArgs {
   const unsigned char* blob;     // packed mechanism (global, 16-byte aligned)
@@ -67,6 +72,8 @@ struct AdvanceArgs {
   unsigned char* cont_key;       // [cont_cap] their remaining-work bucket
   int* cont_sorted;              // [cont_cap] the same slots, longest remaining first: the input of
                                  //   round 0, later of even rounds
+  int probe_att = kProbeAttempts;   // attempts per cell in the probe pass
+  int round_att = kRoundAttempts;   // attempts per cell and continuation round
 };
 
 constexpr int kMaxBoxes = 4096;
@@ -131,13 +138,12 @@ constexpr int kFlagOrderRate = 4;   // bucket of log2(dt * sum_k |dY_k/dt|) at t
 constexpr int kFlagOrderPrev = 8;   // bucket of log2 of the cell's substep count of the previous call
 constexpr int kFlagTwoPass = 16;    // two-pass stiff integration
 constexpr int kNumBuckets = 64;
-constexpr int kProbeAttempts = 32;  // implicit steps per cell in the probe pass
-constexpr int kRoundAttempts = 32;  // implicit steps per cell and continuation round
 
 // bytes of continuation state per queue slot
 __host__ __device__ constexpr long long cont_bytes_per_slot(int ns) { return 8LL * (ns + 4) + 12; }
 
 constexpr int kBulkBlock = 128;
-constexpr int kStiffBlock = 128;
+constexpr int kStiffBlock = 128;      // default threads per CTA of the dense stiff kernel
+constexpr int kStiffBlockMax = 256;   // largest CTA the tuner may choose (64, 128 or 256)
 
 }  // namespace chem

@@ -152,12 +152,12 @@ extern "C" int chem_advance_noalloc(const chem_mechanism* mech, const chem_param
     a.cont_sorted = nullptr;
     int bpsm = 1, spsm = 1;
     if (bulk_occupancy(mech->ns, false, bytes, &bpsm) != 0 || bpsm < 1) bpsm = 1;
-    if (stiff_occupancy(mech->ns, bytes, &spsm) != 0 || spsm < 1) spsm = 1;
+    if (stiff_occupancy(mech->ns, bytes, kStiffBlock, &spsm) != 0 || spsm < 1) spsm = 1;
     long long want = (n + kBulkBlock - 1) / kBulkBlock;
     const long long cap = static_cast<long long>(slot->sms) * bpsm;
     const int bgrid = static_cast<int>(want < cap ? (want < 1 ? 1 : want) : cap);
     int r1 = launch_bulk_f32(mech->ns, a, bgrid, st);
-    int r2 = r1 ? r1 : launch_stiff_f32(mech->ns, a, slot->sms * spsm, st);
+    int r2 = r1 ? r1 : launch_stiff_f32(mech->ns, a, slot->sms * spsm, kStiffBlock, st);
     if (r1 == -1 || r2 == -1) return CHEM_EUNSUPPORTED;
     if (r1 || r2) return fail(static_cast<cudaError_t>(r1 ? r1 : r2), "kernel launch");
   }

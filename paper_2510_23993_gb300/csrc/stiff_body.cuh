@@ -307,9 +307,9 @@ __host__ __device__ constexpr unsigned long long stiff_matrix_bytes(int nj, int 
   return static_cast<unsigned long long>(nj) * (nj + 1) * block * 8ull;
 }
 
-// The kernel body.  smem: dynamic shared memory; tab_pad: bytes at its start taken by the staged
-// tables (0 for a policy with compiled-in constants).
-template <class P, typename S>
+// The kernel body (BLK threads per CTA).  smem: dynamic shared memory; tab_pad: bytes at its start
+// taken by the staged tables (0 for a policy with compiled-in constants).
+template <class P, typename S, int BLK>
 __device__ __forceinline__ void stiff_body(const AdvanceArgs<S>& a, const P& m, unsigned char* smem,
                                            unsigned tab_pad) {
   constexpr int NS = P::NS;
@@ -318,17 +318,17 @@ __device__ __forceinline__ void stiff_body(const AdvanceArgs<S>& a, const P& m, 
   if (a.nbox > 0) stage_box_offsets(soff, a.box_off, a.nbox);
   Smem<NJ> sm;
   sm.t = threadIdx.x;
-  sm.B = kStiffBlock;
+  sm.B = BLK;
   sm.M = reinterpret_cast<double*>(smem + tab_pad + box_smem_bytes(a.nbox));
-  sm.V = sm.M + NJ * NJ * kStiffBlock;
+  sm.V = sm.M + NJ * NJ * BLK;
   const int na = m.na();
 
   const int lane = threadIdx.x & 31;
   // probe and single passes take cells from the stiff queue through an atomic head.  The
   // continuation pass runs in rounds.  Round 0 takes the sorted unfinished cells from a shared
   // queue (longest remaining first) and runs them to completion until the queue is empty; from
-  // then on a lane parks its cell after kRoundAttempts more steps.  Round r >= 1 gives every
-  // parked cell up to kRoundAttempts steps and lists those still unfinished for round r + 1; slot
+  // then on a lane parks its cell after a.round_att more steps.  Round r >= 1 gives every
+  // parked cell up to a.round_att steps and lists those still unfinished for round r + 1; slot
   // q of its list belongs to lane q % 32 of warp q / 32 mod W, warps numbered across the CTAs
   // first, so that the cells still running fill whole warps spread over all SMs.
   const int pass = a.pass;
@@ -370,7 +370,7 @@ __device__ __forceinline__ void stiff_body(const AdvanceArgs<S>& a, const P& m, 
         long long q;
         if (pass == 2 && round > 0) {
           const long long wg = static_cast<long long>(threadIdx.x >> 5) * gridDim.x + blockIdx.x;
-          q = (wg + static_cast<long long>(kr) * gridDim.x * (kStiffBlock / 32)) * 32 + lane;
+          q = (wg + static_cast<long long>(kr) * gridDim.x * (BLK / 32)) * 32 + lane;
           ++kr;
         } else {
           q = base + __popc(needm & ((1u << lane) - 1u));
@@ -582,7 +582,7 @@ __device__ __forceinline__ void stiff_body(const AdvanceArgs<S>& a, const P& m, 
       if (nst >= a.prm.k_max || natt >= 4 * a.prm.k_max) { failed = true; flags |= kFlagMaxSteps; }
     }
     if (!finished && !failed &&
-        ((pass == 1 && natt >= kProbeAttempts) || (pass == 2 && natt_r >= kRoundAttempts))) {
+        ((pass == 1 && natt >= a.probe_att) || (pass == 2 && natt_r >= a.round_att))) {
       // park the cell with its integration state (probe pass: for the sort and round 0; later:
       // for the next round)
 #pragma unroll

@@ -3,7 +3,11 @@
 // The paper tuned its bulk-step count (K_max = 5) and its bulk-to-sparse threshold by hand
 // (Sec. 3.2, App. D).  Here the knobs are the explicit bulk substeps per cell (k_bulk), the
 // order in which stiff cells are handed to the persistent kernel (none, by rate, by rate with the
-// two-pass probe/continuation schedule), and the resident blocks per SM of both kernels.  The tuner times chem_advance on the caller's field for each candidate
+// two-pass probe/continuation schedule), the resident blocks per SM of both kernels, and for the
+// dense stiff kernel its CTA size (64, 128 or 256 threads, one cell per thread) and the
+// scheduling quantum of the two-pass schedule (attempts per cell in the probe pass and in each
+// continuation round: 16, 32 or 64).  None of them changes a cell's result, only the launch
+// shape and the order of work.  The tuner times chem_advance on the caller's field for each candidate
 // (coordinate descent, best of two repetitions, inputs restored between trials), keeps the
 // fastest, and can cache the choice in a text file keyed by mechanism shape, field size and GPU.
 #include <cmath>
@@ -20,6 +24,8 @@ namespace chem {
 void ctx_get_launch(const chem_ctx* c, int* bulk_grid, int* stiff_grid, int* sms, int* ns, int* nr);
 void ctx_set_launch(chem_ctx* c, int bulk_grid, int stiff_grid);
 void ctx_get_params(const chem_ctx* c, chem_params* p);
+void ctx_get_sched(const chem_ctx* c, int* stiff_block, int* probe_att, int* round_att, int* large);
+void ctx_set_sched(chem_ctx* c, int stiff_block, int probe_att, int round_att);
 int occupancy_bulk(const chem_ctx* c);
 int occupancy_stiff(const chem_ctx* c);
 }  // namespace chem
@@ -27,7 +33,7 @@ int occupancy_stiff(const chem_ctx* c);
 namespace {
 
 struct Choice {
-  int k_bulk, order_flags, bulk_bpsm, stiff_bpsm;
+  int k_bulk, order_flags, bulk_bpsm, stiff_bpsm, stiff_block, quantum;
 };
 
 std::string cache_key(int ns, int nr, int64_t n, double dt) {
@@ -54,8 +60,8 @@ bool cache_lookup(const char* path, const std::string& key, Choice* c) {
     const char* bar = std::strstr(line, " | ");
     if (!bar || std::string(line, bar - line) != key) continue;
     Choice t;
-    if (std::sscanf(bar + 3, "k_bulk=%d order=%d bulk_bpsm=%d stiff_bpsm=%d", &t.k_bulk, &t.order_flags, &t.bulk_bpsm,
-                    &t.stiff_bpsm) == 4) {
+    if (std::sscanf(bar + 3, "k_bulk=%d order=%d bulk_bpsm=%d stiff_bpsm=%d stiff_block=%d quantum=%d", &t.k_bulk,
+                    &t.order_flags, &t.bulk_bpsm, &t.stiff_bpsm, &t.stiff_block, &t.quantum) == 6) {
       *c = t;
       found = true;   // the last matching line wins
     }
@@ -68,8 +74,8 @@ void cache_store(const char* path, const std::string& key, const Choice& c) {
   if (!path) return;
   FILE* f = std::fopen(path, "a");
   if (!f) return;
-  std::fprintf(f, "%s | k_bulk=%d order=%d bulk_bpsm=%d stiff_bpsm=%d\n", key.c_str(), c.k_bulk, c.order_flags,
-               c.bulk_bpsm, c.stiff_bpsm);
+  std::fprintf(f, "%s | k_bulk=%d order=%d bulk_bpsm=%d stiff_bpsm=%d stiff_block=%d quantum=%d\n", key.c_str(),
+               c.k_bulk, c.order_flags, c.bulk_bpsm, c.stiff_bpsm, c.stiff_block, c.quantum);
   std::fclose(f);
 }
 
@@ -85,6 +91,8 @@ extern "C" int chem_tune(chem_ctx* ctx, float* T, float* p, float* Y, int64_t ld
   ctx_get_launch(ctx, &bulk_grid0, &stiff_grid0, &sms, &ns, &nr);
   chem_params prm0;
   ctx_get_params(ctx, &prm0);
+  int block0, probe0, round0, large;
+  ctx_get_sched(ctx, &block0, &probe0, &round0, &large);
   const int occ_b = occupancy_bulk(ctx), occ_s = occupancy_stiff(ctx);
   std::memset(out, 0, sizeof(*out));
   const std::string key = cache_key(ns, nr, n, dt);
@@ -96,16 +104,19 @@ extern "C" int chem_tune(chem_ctx* ctx, float* T, float* p, float* Y, int64_t ld
       p.flags &= ~CHEM_FLAG_TWO_PASS;
       chem_set_params(ctx, &p);
     }
+    ctx_set_sched(ctx, c.stiff_block, c.quantum, c.quantum);
     ctx_set_launch(ctx, sms * c.bulk_bpsm, sms * c.stiff_bpsm);
   };
   Choice best{prm0.k_bulk, prm0.flags & (CHEM_FLAG_ORDER_RATE | CHEM_FLAG_ORDER_PREV | CHEM_FLAG_TWO_PASS),
-              bulk_grid0 / sms, stiff_grid0 / sms};
+              bulk_grid0 / sms, stiff_grid0 / sms, block0, probe0};
   if (cache_lookup(cache_path, key, &best)) {
     apply(best);
     out->k_bulk = best.k_bulk;
     out->flags = best.order_flags;
     out->bulk_blocks_per_sm = best.bulk_bpsm;
     out->stiff_blocks_per_sm = best.stiff_bpsm;
+    out->stiff_block = best.stiff_block;
+    out->quantum = best.quantum;
     out->from_cache = 1;
     return CHEM_OK;
   }
@@ -185,6 +196,25 @@ extern "C" int chem_tune(chem_ctx* ctx, float* T, float* p, float* Y, int64_t ld
       c.bulk_bpsm = b;
       consider(c);
     }
+  if (!large) {
+    // CTA size of the stiff kernel, each with the most resident blocks that fit
+    for (int blk : {64, 128, 256})
+      if (blk != best.stiff_block) {
+        Choice c = best;
+        c.stiff_block = blk;
+        ctx_set_sched(ctx, blk, c.quantum, c.quantum);
+        c.stiff_bpsm = occupancy_stiff(ctx);
+        consider(c);
+      }
+    // scheduling quantum of the two-pass schedule
+    if (best.order_flags & CHEM_FLAG_TWO_PASS)
+      for (int qa : {16, 32, 64})
+        if (qa != best.quantum) {
+          Choice c = best;
+          c.quantum = qa;
+          consider(c);
+        }
+  }
   apply(best);
   restore();   // leave the caller's state as it came in
   cudaStreamSynchronize(st);
@@ -197,6 +227,8 @@ extern "C" int chem_tune(chem_ctx* ctx, float* T, float* p, float* Y, int64_t ld
   out->flags = best.order_flags;
   out->bulk_blocks_per_sm = best.bulk_bpsm;
   out->stiff_blocks_per_sm = best.stiff_bpsm;
+  out->stiff_block = best.stiff_block;
+  out->quantum = best.quantum;
   out->best_ms = t_best;
   out->default_ms = t_default;
   return CHEM_OK;

@@ -28,7 +28,9 @@ def test_tune_then_advance(h2mech, tmp_path):
     cache = str(tmp_path / "tune.txt")
     res = ctx.tune(tT, tp, tY, trho, te, 1e-8, sub, cache_path=cache)
     assert res["from_cache"] == 0 and res["trials"] >= 2
-    assert 1 <= res["k_bulk"] <= 3 and res["flags"] in (0, chem.CHEM_FLAG_ORDER_RATE)
+    assert 1 <= res["k_bulk"] <= 3
+    assert res["flags"] in (0, chem.CHEM_FLAG_ORDER_RATE, chem.CHEM_FLAG_ORDER_RATE | chem.CHEM_FLAG_TWO_PASS)
+    assert res["stiff_block"] in (64, 128, 256) and res["quantum"] in (16, 32, 64)
     assert res["best_ms"] <= res["default_ms"]
     assert np.array_equal(tT.cpu().numpy(), T) and np.array_equal(tY.cpu().numpy(), Y)   # inputs restored
     ctx.advance(tT, tp, tY, trho, te, 1e-8, sub)
@@ -46,6 +48,40 @@ def test_tune_then_advance(h2mech, tmp_path):
     ctx2 = chem.Context(h2mech, max_cells=n)
     res2 = ctx2.tune(tT, tp, tY, trho, te, 1e-8, sub, cache_path=cache)
     assert res2["from_cache"] == 1 and res2["trials"] == 0
-    assert (res2["k_bulk"], res2["flags"], res2["stiff_blocks_per_sm"]) == (res["k_bulk"], res["flags"], res["stiff_blocks_per_sm"])
+    keys = ("k_bulk", "flags", "stiff_blocks_per_sm", "stiff_block", "quantum")
+    assert tuple(res2[k] for k in keys) == tuple(res[k] for k in keys)
     ctx.close()
     ctx2.close()
+
+
+def test_launch_shape_leaves_results_unchanged(h2mech, tmp_path):
+    """Every stiff CTA size and two-pass scheduling quantum the tuner can pick gives the same bits:
+    each configuration is applied through a hand-written cache line (no trials) and one step of the
+    same field is advanced under it."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    chem.build()
+    T, p, Y, hot = synth.sheet_field(h2mech, n=24, seed=9, frac=0.08)
+    T, p, Y = T.astype(np.float32), p.astype(np.float32), np.ascontiguousarray(Y, dtype=np.float32)
+    rho, e = oracle.state_from_TpY(h2mech, T, p, Y)
+    rho, e = rho.astype(np.float32), e.astype(np.float32)
+    n, dt = T.size, 1e-8
+    dev = torch.cuda.get_device_name(0).replace(" ", "_")
+    key = "ns=%d nr=%d log2n=%d dt=%.3e dev=%s" % (h2mech["ns"], h2mech["nr"], int(np.floor(np.log2(n))), dt, dev)
+    results = []
+    for blk, q in ((128, 32), (64, 16), (256, 64), (128, 16)):
+        cache = tmp_path / f"c{blk}_{q}.txt"
+        cache.write_text(f"{key} | k_bulk=1 order={chem.CHEM_FLAG_ORDER_RATE | chem.CHEM_FLAG_TWO_PASS} "
+                         f"bulk_bpsm=2 stiff_bpsm=1 stiff_block={blk} quantum={q}\n")
+        ctx = chem.Context(h2mech, max_cells=n)
+        tT, tp, tY, trho, te = (torch.from_numpy(np.ascontiguousarray(a)).to(DEV) for a in (T, p, Y, rho, e))
+        sub = torch.zeros(n, dtype=torch.int32, device=DEV)
+        res = ctx.tune(tT, tp, tY, trho, te, dt, sub, cache_path=str(cache))
+        assert res["from_cache"] == 1 and (res["stiff_block"], res["quantum"]) == (blk, q)
+        ctx.advance(tT, tp, tY, trho, te, dt, sub)
+        st = ctx.status()
+        assert st["status"] == 0 and st["nqueued"] == int(hot.sum())
+        results.append((tT.cpu().numpy(), tY.cpu().numpy(), sub.cpu().numpy()))
+        ctx.close()
+    for r in results[1:]:
+        assert all(np.array_equal(a, b) for a, b in zip(results[0], r))
