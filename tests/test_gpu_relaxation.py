@@ -65,8 +65,9 @@ def test_relaxation_histories_match_oracle(h2mech):
         assert st["status"] == 0
         T_gpu.append(tT.cpu().numpy().astype(np.float64))
     T_gpu = np.array(T_gpu)
-    # every point of the five histories, and the characteristic times
-    assert np.all(np.abs(T_gpu - T_ref) / T_ref <= 2e-4), np.abs(T_gpu - T_ref).max()
+    # every point of the five histories at the contract's 1e-4 (measured: within 3e-7), and the
+    # characteristic times
+    assert np.all(np.abs(T_gpu - T_ref) / T_ref <= 1e-4), (np.abs(T_gpu - T_ref) / T_ref).max()
     assert np.all(np.abs(T_ref[-1] - T0) > 10.0)   # a real relaxation happened (14 to 880 K)
     for j in range(5):
         th_ref = _half_time(grid, T_ref[:, j], T0[j])
