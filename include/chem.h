@@ -109,11 +109,15 @@ typedef struct {
   int64_t nfailed;    /* stiff cells that hit k_max or whose step size collapsed */
   int64_t ninvalid;   /* non-finite or non-physical inputs (count -1, state untouched) */
   int64_t substeps;   /* total implicit substeps of the stiff cells */
-  int64_t attempts;   /* attempted implicit steps (accepted + rejected): Jacobian + LU each */
+  int64_t attempts;   /* attempted implicit steps (accepted + rejected) */
   int64_t newton;     /* Newton iterations of the stage solves (rates + T(e) + solve each) */
   int32_t status;     /* CHEM_OK or the most severe per-cell error code */
   float bulk_ms;      /* bulk kernel duration (CHEM_FLAG_TIMING), else 0 */
   float stiff_ms;     /* stiff kernel duration (CHEM_FLAG_TIMING), else 0 */
+  int64_t factorizations; /* Jacobians formed and iteration matrices factored: one per attempt in
+                             the one-thread-per-cell kernel; the warp-per-cell kernel of the large
+                             mechanisms keeps a factored matrix over up to 8 steps of unchanged
+                             size */
 } chem_stats;
 
 /* Defaults: rtol 1e-5, atol 1e-10, T_min 0, bulk_frac 0.05, y_floor 1e-10, k_bulk 1,

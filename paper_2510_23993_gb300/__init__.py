@@ -70,7 +70,8 @@ class chem_stats(ctypes.Structure):
     _fields_ = [("ncell", ctypes.c_int64), ("nskipped", ctypes.c_int64), ("nbulk", ctypes.c_int64),
                 ("nqueued", ctypes.c_int64), ("nfailed", ctypes.c_int64), ("ninvalid", ctypes.c_int64),
                 ("substeps", ctypes.c_int64), ("attempts", ctypes.c_int64), ("newton", ctypes.c_int64),
-                ("status", ctypes.c_int32), ("bulk_ms", ctypes.c_float), ("stiff_ms", ctypes.c_float)]
+                ("status", ctypes.c_int32), ("bulk_ms", ctypes.c_float), ("stiff_ms", ctypes.c_float),
+                ("factorizations", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

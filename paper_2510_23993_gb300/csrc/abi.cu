@@ -690,6 +690,8 @@ int chem_status(chem_ctx* ctx, void* stream, chem_stats* out) {
   out->substeps = static_cast<int64_t>(w.substeps);
   out->attempts = static_cast<int64_t>(w.attempts);
   out->newton = static_cast<int64_t>(w.newton);
+  // the dense stiff kernel factors on every attempt; the large one counts what it factors
+  out->factorizations = ctx->large ? static_cast<int64_t>(w.factorizations) : out->attempts;
   out->bulk_ms = 0.0f;
   out->stiff_ms = 0.0f;
   if (ctx->timed) {

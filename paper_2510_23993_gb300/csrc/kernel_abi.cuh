@@ -14,6 +14,7 @@ struct Workspace {
   int rc[3];                     // two-pass mode: cells left after continuation round r, in rc[r % 3]
   unsigned bar_count, bar_gen;   // grid barrier of the continuation rounds
   unsigned long long nskipped, nbulk, ninvalid, nfailed, substeps, attempts, newton;
+  unsigned long long factorizations;   // LU factorisations (the large kernel reuses some across steps)
 };
 
 struct KParams {

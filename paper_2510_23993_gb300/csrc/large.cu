@@ -29,6 +29,12 @@ constexpr int kStiffWarps = 5;   // cells in flight per CTA of the stiff kernel 
 constexpr int kBulkWarps = 8;    // cells in flight per CTA of the bulk kernel
 constexpr int kNewtMax = 6;
 constexpr double kNewtTol = 0.03;
+// reuse of the factored iteration matrix across steps (stiff_kernel_lg): hold h while the
+// controller's growth factor is within [1, kHoldMax] and the Newton contraction estimate
+// eta = theta / (1 - theta) is at most kEtaReuse, for at most kLuMaxAge steps per factorisation
+constexpr double kHoldMax = 1.2;
+constexpr double kEtaReuse = 0.1;
+constexpr int kLuMaxAge = 8;
 // Alexander's L-stable DIRK3 (as in stiff.cu)
 constexpr double kG = 0.43586652150845895;
 constexpr double kA21 = 0.5 * (1.0 - kG);
@@ -721,7 +727,7 @@ __global__ void __launch_bounds__(32 * kStiffWarps) stiff_kernel_lg(const Advanc
   CellCtx c;
   c.rtol = a.prm.rtol;
   c.atol = a.prm.atol;
-  unsigned long long c_sub = 0, c_fail = 0, c_att = 0, c_newt = 0;
+  unsigned long long c_sub = 0, c_fail = 0, c_att = 0, c_newt = 0, c_lu = 0;
   int flags = 0;
 #pragma unroll 1
   while (true) {
@@ -759,19 +765,32 @@ __global__ void __launch_bounds__(32 * kStiffWarps) stiff_kernel_lg(const Advanc
     double t = 0.0, h = 1e-6 * dt, eta_cell = 1.0;
     int nst = 0, natt = 0;
     bool finished = false, failed = false;
+    // the factored iteration matrix of the last attempt, reused while the step size is held and
+    // Newton keeps contracting fast (the 53 x 53 LU is most of an attempt's FP64 work)
+    bool lu_valid = false;
+    double h_lu = 0.0;
+    int lu_age = 0;
 #pragma unroll 1
     while (!finished && !failed) {
       ++natt;
       ++c_att;
       const double gh = kG * h;
-      {
+      const bool reuse = lu_valid && h == h_lu && lu_age < kLuMaxAge;
+      bool conv = true;
+      if (reuse) {
+        ++lu_age;
+      } else {
         float Yf[2];
 #pragma unroll
         for (int kk = 0; kk < 2; ++kk) Yf[kk] = static_cast<float>(y[kk]);
         warp_jacobian<NS>(m, s, c.rho, static_cast<float>(Tc), Yf, cvR);
         warp_iteration_matrix<NS>(s, gh);
+        conv = warp_lu<NS>(s);
+        ++c_lu;
+        lu_valid = conv;
+        h_lu = h;
+        lu_age = 0;
       }
-      bool conv = warp_lu<NS>(s);
       double hk1[2] = {0.0, 0.0}, hk2[2] = {0.0, 0.0}, z[2], base[2];
       double Tz = Tc, eta = eta_cell;
 #pragma unroll 1
@@ -796,7 +815,10 @@ __global__ void __launch_bounds__(32 * kStiffWarps) stiff_kernel_lg(const Advanc
       }
       eta_cell = fmax(eta, 0.05);
       if (!conv) {
-        h *= 0.25;
+        // Newton failed: with a reused (older) iteration matrix retry the same step with a fresh
+        // Jacobian, otherwise shrink the step
+        if (!reuse) h *= 0.25;
+        lu_valid = false;
         eta_cell = 1.0;
       } else {
         double er[2];
@@ -835,7 +857,9 @@ __global__ void __launch_bounds__(32 * kStiffWarps) stiff_kernel_lg(const Advanc
         }
         double fac = 0.9 * rcbrt(fmax(static_cast<double>(err), 1e-12));
         fac = fmin(5.0, fmax(0.2, fac));
-        h *= fac;
+        // hold the step size (and so the factored matrix) when the controller would grow it by at
+        // most kHoldMax and Newton contracts fast; any other factor refactors at the next attempt
+        if (!(err <= 1.0f && fac >= 1.0 && fac <= kHoldMax && eta <= kEtaReuse)) h *= fac;
       }
       if (!finished) {
         if (t + h > dt) h = dt - t;
@@ -876,6 +900,7 @@ __global__ void __launch_bounds__(32 * kStiffWarps) stiff_kernel_lg(const Advanc
   if (lane == 0) {
     if (c_att) atomicAdd(&a.ws->attempts, c_att);
     if (c_newt) atomicAdd(&a.ws->newton, c_newt);
+    if (c_lu) atomicAdd(&a.ws->factorizations, c_lu);
     if (c_sub) atomicAdd(&a.ws->substeps, c_sub);
     if (c_fail) atomicAdd(&a.ws->nfailed, c_fail);
     if (flags) atomicOr(&a.ws->status, flags);

@@ -176,6 +176,7 @@ extern "C" int chem_advance_noalloc(const chem_mechanism* mech, const chem_param
     stats->substeps = static_cast<int64_t>(w.substeps);
     stats->attempts = static_cast<int64_t>(w.attempts);
     stats->newton = static_cast<int64_t>(w.newton);
+    stats->factorizations = stats->attempts;   // the dense stiff kernel factors on every attempt
     int status = CHEM_OK;
     if (w.status & kFlagInvalid) status = CHEM_EINVAL;
     if (w.status & (kFlagNoConv | kFlagTemp)) status = CHEM_ENOCONV;
