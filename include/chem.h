@@ -116,7 +116,7 @@ typedef struct {
   float stiff_ms;     /* stiff kernel duration (CHEM_FLAG_TIMING), else 0 */
   int64_t factorizations; /* Jacobians formed and iteration matrices factored: one per attempt in
                              the one-thread-per-cell kernel; the warp-per-cell kernel of the large
-                             mechanisms keeps a factored matrix over up to 8 steps of unchanged
+                             mechanisms keeps a factored matrix over up to 16 steps of unchanged
                              size */
 } chem_stats;
 

@@ -34,7 +34,7 @@ constexpr double kNewtTol = 0.03;
 // eta = theta / (1 - theta) is at most kEtaReuse, for at most kLuMaxAge steps per factorisation
 constexpr double kHoldMax = 1.2;
 constexpr double kEtaReuse = 0.1;
-constexpr int kLuMaxAge = 8;
+constexpr int kLuMaxAge = 16;
 // Alexander's L-stable DIRK3 (as in stiff.cu)
 constexpr double kG = 0.43586652150845895;
 constexpr double kA21 = 0.5 * (1.0 - kG);
