@@ -55,6 +55,7 @@ def _run(ctx, T, p, Y, rho, e, dt, ld=None):
     sub = torch.full((n,), -99, dtype=torch.int32, device=DEV)
     rc = chem.chem_advance(ctx.handle, tT, tp, tY, tY.stride(0), trho, te, n, dt, sub)
     st = ctx.status()
+    assert st["factorizations"] == st["attempts"]   # one thread per cell: one LU per attempted step
     Yo = tY.cpu().numpy()
     if ld is not None:
         assert np.all(Yo[:, n:] == -7.0)   # padding untouched
