@@ -268,6 +268,7 @@ def run_gpu(args, rank, world, local_rank, dist):
             "clocks": clk, "tuned": tuned,
             "stiff": {"queued_cells": stats[-1]["nqueued"], "bulk_cells": stats[-1]["nbulk"],
                       "substeps_per_stiff_cell": stats[-1]["substeps"] / max(1, stats[-1]["nqueued"]),
+                      "attempts_per_substep": stats[-1]["attempts"] / max(1, stats[-1]["substeps"]),
                       "newton_per_attempt": stats[-1]["newton"] / max(1, stats[-1]["attempts"]),
                       "factorizations_per_attempt": stats[-1]["factorizations"] / max(1, stats[-1]["attempts"])}}
     if args.gated:   # the surrogate is compiled for the 9- and the 53-species mechanisms
