@@ -233,7 +233,8 @@ void ctx_get_sched(const chem_ctx* c, int* stiff_block, int* probe_att, int* rou
   *large = c->large ? 1 : 0;
 }
 void ctx_set_sched(chem_ctx* c, int stiff_block, int probe_att, int round_att) {
-  if (stiff_block >= 32 && stiff_block <= kStiffBlockMax && stiff_block % 32 == 0) c->stiff_block = stiff_block;
+  // the CTA sizes the stiff kernel is compiled for; anything else keeps the current one
+  if (stiff_block == 64 || stiff_block == 128 || stiff_block == 256) c->stiff_block = stiff_block;
   if (probe_att >= 1) c->probe_att = probe_att;
   if (round_att >= 1) c->round_att = round_att;
 }

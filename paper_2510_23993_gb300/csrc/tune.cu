@@ -62,8 +62,12 @@ bool cache_lookup(const char* path, const std::string& key, Choice* c) {
     Choice t;
     if (std::sscanf(bar + 3, "k_bulk=%d order=%d bulk_bpsm=%d stiff_bpsm=%d stiff_block=%d quantum=%d", &t.k_bulk,
                     &t.order_flags, &t.bulk_bpsm, &t.stiff_bpsm, &t.stiff_block, &t.quantum) == 6) {
-      *c = t;
-      found = true;   // the last matching line wins
+      // a hand-edited line with a CTA size or quantum the kernel does not offer is ignored
+      if ((t.stiff_block == 64 || t.stiff_block == 128 || t.stiff_block == 256) && t.quantum >= 1 &&
+          t.quantum <= 1024 && t.stiff_bpsm >= 1 && t.bulk_bpsm >= 1) {
+        *c = t;
+        found = true;   // the last matching line wins
+      }
     }
   }
   std::fclose(f);
