@@ -3,7 +3,8 @@
 Same parity bar as the warp-per-cell rates of test_gpu_large.py (relative 1e-4 of the net rate,
 or a few FP32 ulps of the gross rate): against the FP64 oracle at sizes that span several
 128-cell tiles and a ragged tail, on a strided sample of a 1,048,576-cell batch (the size the rate
-study times), on cells whose log-rates leave the FP32 range (the FP64 fallback), with a leading
+study times), below, above and across the thermo fit range (the per-regime reaction records), on
+cells whose rates of progress leave the FP32 range (the FP64 fallback), with a leading
 dimension larger than the cell count, and on degenerate inputs (no cells, one cell, species at
 exactly zero).  Also: results are deterministic, and a 9-species context reports the call as
 unsupported.
@@ -61,6 +62,24 @@ def _run(ctx, rho, T, Y):
 @pytest.mark.parametrize("n", [1, 127, 128, 129, 500, 1000])
 def test_rates_tc_parity(hcmech, n):
     T, Y, rho = _state(hcmech, n, seed=n, zero_frac=0.1)
+    ctx = chem.Context(hcmech, max_cells=n)
+    f = _run(ctx, rho, T, Y)
+    assert np.all(np.isfinite(f))
+    assert np.all(_bar(hcmech, rho, T, Y, f))
+    ctx.close()
+
+
+@pytest.mark.parametrize("T_lo,T_hi", [(150.0, 299.0), (3600.0, 5500.0), (250.0, 4000.0)])
+def test_rates_tc_thermo_regimes(hcmech, T_lo, T_hi):
+    """Below, above and across the thermo fit range [300, 3500] K: the kernel takes the reaction
+    records of each cell's regime (cp frozen outside the range, h and s continuous)."""
+    n = 640
+    rng = np.random.default_rng(int(T_lo))
+    T = rng.uniform(T_lo, T_hi, n).astype(np.float32)
+    p = (rng.uniform(0.5, 20, n) * synth.P_ATM).astype(np.float32)
+    Y = np.ascontiguousarray(rng.dirichlet(np.full(hcmech["ns"], 0.3), size=n).T, dtype=np.float32)
+    rho, _ = oracle.state_from_TpY(hcmech, T, p, Y)
+    rho = rho.astype(np.float32)
     ctx = chem.Context(hcmech, max_cells=n)
     f = _run(ctx, rho, T, Y)
     assert np.all(np.isfinite(f))
