@@ -784,11 +784,22 @@ def run_study(args):
         t_f = _time_ms(lambda: ctx.rates(rho, tT, tY, f), args.steps, torch)
         t_m = _time_ms(lambda: mk.rates(rho, tT, tY, f), args.steps, torch)
         hbm = (2 * mech["ns"] + 2) * 4 * N      # Y read, dY/dt written, rho and T read
+        # tensor-core work as issued: K padded to 64 species, N to 336 reactions, three BF16 parts
+        # of each FP32 operand (six split pairs for the efficiencies)
+        nrp, ntb = 336, 32
+        issued = N * (2 * 64 * ntb * 6 + 2 * 3 * 2 * 64 * nrp + 3 * 2 * nrp * 64)
+        peaks = os.path.join(ROOT, "MEASURED_PEAKS.json")
+        pk = json.load(open(peaks)) if os.path.exists(peaks) else {}
+        tf = issued / (t_c / 1e3) / 1e12
+        gbs = hbm / (t_c / 1e3) / 1e9
         print(json.dumps({"study": "rates_tc", "mechanism": "53 species / 325 reactions", "cells": N,
                           "tensor_core_ms": t_c, "fused_ms": t_f, "multikernel_ms": t_m,
                           "tensor_core_cells_per_s": N / (t_c / 1e3), "fused_over_tensor_core": t_f / t_c,
                           "multikernel_over_tensor_core": t_m / t_c,
-                          "tensor_core_hbm_GB_s": hbm / (t_c / 1e3) / 1e9}), flush=True)
+                          "tensor_issued_TFLOP_s": tf,
+                          "frac_of_measured_bf16": tf / pk["bf16_tflops"] if pk.get("bf16_tflops") else None,
+                          "tensor_core_hbm_GB_s": gbs,
+                          "frac_of_measured_hbm": gbs / pk["hbm_gbs"] if pk.get("hbm_gbs") else None}), flush=True)
         mk.close()
         ctx.close()
         return
