@@ -544,9 +544,10 @@ struct CellCtx {
 // stage equation z = yb + hh f(z) by simplified Newton (as stage_newton in stiff.cu)
 template <int NS>
 __device__ bool warp_stage_newton(const LView& m, const Scratch& s, const CellCtx& c, const double (&yb)[2],
-                                  double hh, double (&z)[2], double& Tz, double& eta, unsigned long long& n_it) {
+                                  double hh, double (&z)[2], double& Tz, float& eta, unsigned long long& n_it) {
   const int lane = threadIdx.x & 31;
-  double prev = 0.0;
+  // the convergence control (norm, contraction rate) is FP32: it only decides when to stop
+  float prev = 0.0f;
 #pragma unroll 1
   for (int it = 0; it < kNewtMax; ++it) {
     ++n_it;
@@ -574,14 +575,14 @@ __device__ bool warp_stage_newton(const LView& m, const Scratch& s, const CellCt
         ss = fmaf(r, r, ss);
       }
     }
-    const double nrm = sqrt(static_cast<double>(wsum(ss)) * (1.0 / NS));
+    const float nrm = sqrtf(wsum(ss) * (1.0f / NS));
     if (!(nrm == nrm)) return false;
     if (it > 0) {
-      const double theta = nrm / prev;
-      if (theta >= 1.0) return nrm <= 0.5 && theta < 2.0;
-      eta = theta / (1.0 - theta);
+      const float theta = nrm / prev;
+      if (theta >= 1.0f) return nrm <= 0.5f && theta < 2.0f;
+      eta = theta / (1.0f - theta);
     }
-    if (eta * nrm <= kNewtTol || nrm <= 1e-3) return true;
+    if (eta * nrm <= static_cast<float>(kNewtTol) || nrm <= 1e-3f) return true;
     prev = nrm;
   }
   return false;
@@ -762,7 +763,8 @@ __global__ void __launch_bounds__(32 * kStiffWarps) stiff_kernel_lg(const Advanc
         continue;
       }
     }
-    double t = 0.0, h = 1e-6 * dt, eta_cell = 1.0;
+    double t = 0.0, h = 1e-6 * dt;
+    float eta_cell = 1.0f;
     int nst = 0, natt = 0;
     bool finished = false, failed = false;
     // the factored iteration matrix of the last attempt, reused while the step size is held and
@@ -792,7 +794,8 @@ __global__ void __launch_bounds__(32 * kStiffWarps) stiff_kernel_lg(const Advanc
         lu_age = 0;
       }
       double hk1[2] = {0.0, 0.0}, hk2[2] = {0.0, 0.0}, z[2], base[2];
-      double Tz = Tc, eta = eta_cell;
+      double Tz = Tc;
+      float eta = eta_cell;
 #pragma unroll 1
       for (int st = 0; st < 3 && conv; ++st) {
         const double a1 = st == 1 ? kA21 : (st == 2 ? kB1 : 0.0);
@@ -813,13 +816,13 @@ __global__ void __launch_bounds__(32 * kStiffWarps) stiff_kernel_lg(const Advanc
           }
         }
       }
-      eta_cell = fmax(eta, 0.05);
+      eta_cell = fmaxf(eta, 0.05f);
       if (!conv) {
         // Newton failed: with a reused (older) iteration matrix retry the same step with a fresh
         // Jacobian, otherwise shrink the step
         if (!reuse) h *= 0.25;
         lu_valid = false;
-        eta_cell = 1.0;
+        eta_cell = 1.0f;
       } else {
         double er[2];
 #pragma unroll
@@ -828,14 +831,16 @@ __global__ void __launch_bounds__(32 * kStiffWarps) stiff_kernel_lg(const Advanc
           er[kk] = (kB1 - kBh1) * hk1[kk] + (kB2 - kBh2) * hk2[kk] + kG * hk3;
         }
         warp_solve<NS>(s, er);
+        // the weighted error norm is a step-size control quantity: FP32
         float errl = 0.0f;
 #pragma unroll
         for (int kk = 0; kk < 2; ++kk) {
           if (lane + 32 * kk < NS) {
-            const double w = static_cast<double>(c.atol) + static_cast<double>(c.rtol) * fmax(fabs(y[kk]), fabs(z[kk]));
-            errl = fmaxf(errl, static_cast<float>(fabs(er[kk]) / w));
+            const float zk = static_cast<float>(z[kk]);
+            const float w = c.atol + c.rtol * fmaxf(fabsf(static_cast<float>(y[kk])), fabsf(zk));
+            errl = fmaxf(errl, fabsf(static_cast<float>(er[kk])) / w);
             // a clearly negative mass fraction rejects the step (see stiff.cu)
-            if (z[kk] < -10.0 * static_cast<double>(c.atol)) errl = fmaxf(errl, 4.0f);
+            if (zk < -10.0f * c.atol) errl = fmaxf(errl, 4.0f);
           }
         }
         float err = wmax(errl);
@@ -855,11 +860,12 @@ __global__ void __launch_bounds__(32 * kStiffWarps) stiff_kernel_lg(const Advanc
             err = 4.0f;
           }
         }
-        double fac = 0.9 * rcbrt(fmax(static_cast<double>(err), 1e-12));
-        fac = fmin(5.0, fmax(0.2, fac));
+        float fac = 0.9f * rcbrtf(fmaxf(err, 1e-12f));
+        fac = fminf(5.0f, fmaxf(0.2f, fac));
         // hold the step size (and so the factored matrix) when the controller would grow it by at
         // most kHoldMax and Newton contracts fast; any other factor refactors at the next attempt
-        if (!(err <= 1.0f && fac >= 1.0 && fac <= kHoldMax && eta <= kEtaReuse)) h *= fac;
+        if (!(err <= 1.0f && fac >= 1.0f && fac <= static_cast<float>(kHoldMax) && eta <= static_cast<float>(kEtaReuse)))
+          h *= static_cast<double>(fac);
       }
       if (!finished) {
         if (t + h > dt) h = dt - t;
