@@ -423,8 +423,10 @@ __device__ __forceinline__ void warp_iteration_matrix(const Scratch& s, double h
   __syncwarp();
 }
 
-// LU with partial pivoting by the warp (unit-lower L, U with its diagonal inverted; s.piv holds
-// the composite row permutation: row k of the factors is row s.piv[k] of the original matrix).
+// LU with partial pivoting by the warp (unit-lower L; U stored as D^-1 U, unit upper, with the
+// reciprocals D^-1 of its pivots on the diagonal; s.piv holds the composite row permutation: row
+// k of the factors is row s.piv[k] of the original matrix).  Scaling U's rows once here lets every
+// solve apply D^-1 to its right-hand side in one step instead of a one-lane multiply per row.
 // Returns false (warp-uniform) for a singular matrix.
 template <int NS>
 __device__ bool warp_lu(const Scratch& s) {
@@ -491,13 +493,20 @@ __device__ bool warp_lu(const Scratch& s) {
     if (lane == 0) M[k * NS + k] = inv;
     __syncwarp();
   }
+  // U -> D^-1 U: row i of the strict upper triangle times its pivot's reciprocal
+#pragma unroll 1
+  for (int i = 0; i < NS - 1; ++i) {
+    const double d = M[i * NS + i];
+    for (int c = i + 1 + lane; c < NS; c += 32) M[i * NS + c] *= d;
+  }
+  __syncwarp();
   return true;
 }
 
 // x = M^-1 b with the factors of warp_lu; b / x: this lane's entries lane and lane + 32.  The
 // permuted right-hand side is gathered through shared memory once; the substitutions then keep
-// x in registers (lane-owned entries) and broadcast each finished entry with a shuffle, in the
-// same order of operations per entry as a column sweep.
+// x in registers (lane-owned entries) and broadcast each finished entry with a shuffle (column
+// sweeps: unit-lower L forward, then the unit upper D^-1 U backward on D^-1 y).
 template <int NS>
 __device__ void warp_solve(const Scratch& s, double (&b)[2]) {
   static_assert(NS <= 64, "two entries per lane");
@@ -524,10 +533,11 @@ __device__ void warp_solve(const Scratch& s, double (&b)[2]) {
     if (i0 > j) x[0] = fma(-M[i0 * NS + j], vj, x[0]);
     if (i1 > j && i1 < NS) x[1] = fma(-M[i1 * NS + j], vj, x[1]);
   }
+  // back substitution with the unit upper factor D^-1 U on D^-1 y
+  x[0] *= M[i0 * NS + i0];
+  if (i1 < NS) x[1] *= M[i1 * NS + i1];
 #pragma unroll 1
   for (int j = NS - 1; j >= 0; --j) {
-    if (i0 == j) x[0] *= M[j * NS + j];
-    if (i1 == j) x[1] *= M[j * NS + j];
     const double vj = __shfl_sync(0xffffffffu, j < 32 ? x[0] : x[1], j & 31);
     if (i0 < j) x[0] = fma(-M[i0 * NS + j], vj, x[0]);
     if (i1 < j) x[1] = fma(-M[i1 * NS + j], vj, x[1]);
