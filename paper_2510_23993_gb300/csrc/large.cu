@@ -428,6 +428,24 @@ __device__ __forceinline__ void warp_iteration_matrix(const Scratch& s, double h
 // k of the factors is row s.piv[k] of the original matrix).  Scaling U's rows once here lets every
 // solve apply D^-1 to its right-hand side in one step instead of a one-lane multiply per row.
 // Returns false (warp-uniform) for a singular matrix.
+// |x| as an unsigned integer: for finite values it orders like |x|, so the pivot search compares
+// integers instead of FP64 values and picks the same pivot
+__device__ __forceinline__ unsigned long long abs_key64(double x) {
+  return static_cast<unsigned long long>(__double_as_longlong(x)) & 0x7fffffffffffffffull;
+}
+
+// 1 / x for a finite nonzero pivot: the hardware approximation (rcp.approx.ftz.f64, relative
+// error below 2^-22 for normal x) and two Newton-Raphson steps r <- r + r (1 - x r), to within
+// an ulp or two of the FP64 reciprocal, in four FMAs instead of a correctly rounded division
+__device__ __forceinline__ double pivot_rcp(double x) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+  double e = fma(-x, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-x, r, 1.0);
+  return fma(r, e, r);
+}
+
 template <int NS>
 __device__ bool warp_lu(const Scratch& s) {
   const int lane = threadIdx.x & 31;
@@ -436,25 +454,27 @@ __device__ bool warp_lu(const Scratch& s) {
   __syncwarp();
 #pragma unroll 1
   for (int k = 0; k < NS; ++k) {
-    double best = -1.0;
-    int p = k;
+    // the pivot search on integer keys of |M_ik| (integer pipe instead of FP64 compares)
+    unsigned long long best = 0ull;
+    int p = NS;
     for (int i = k + lane; i < NS; i += 32) {
-      const double v = fabs(M[i * NS + k]);
-      if (v > best) {
+      const unsigned long long v = abs_key64(M[i * NS + k]);
+      if (p == NS || v > best) {
         best = v;
         p = i;
       }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const unsigned long long ob = __shfl_xor_sync(0xffffffffu, best, o);
       const int op = __shfl_xor_sync(0xffffffffu, p, o);
-      if (ob > best || (ob == best && op < p)) {
+      if (op < NS && (p == NS || ob > best || (ob == best && op < p))) {
         best = ob;
         p = op;
       }
     }
-    if (!(best > 0.0)) return false;
+    // zero pivot or NaN: singular
+    if (best == 0ull || best > 0x7ff0000000000000ull) return false;
     if (p != k) {
       if (lane == 0) {
         const int t = s.piv[k];
@@ -468,7 +488,7 @@ __device__ bool warp_lu(const Scratch& s) {
       }
     }
     __syncwarp();
-    const double inv = 1.0 / M[k * NS + k];
+    const double inv = pivot_rcp(M[k * NS + k]);
     for (int i = k + 1 + lane; i < NS; i += 32) M[i * NS + k] *= inv;
     __syncwarp();
     // rank-1 update of the trailing m x m block, spread over the lanes element by element
