@@ -14,7 +14,10 @@ front of the method (chem_advance_gated), after training it on pairs made by the
 (outside the timed region), and reports the accepted fraction and the sampled error vs the oracle.
 A third leg ("paper_loop") times the paper's own method on the same steps: explicit first-order
 substeps under the relative-change rule of Sec. 2.1, driven by Algorithm 3 (chem_advance_explicit),
-with its sampled error vs the oracle.
+with its sampled error vs the oracle.  Three more objects carry the other workloads: "config2" (the
+400-box AMR hierarchy through the box table, graph-replayed), "config3" (a 16M-cell flat batch,
+plain and gated) and "config4" (the 53-species sheet at 32x32x16, plain and gated); `--no-configs`
+leaves them out, and `--config 3|4` makes either the line's own workload.
 
 Under torchrun (N > 1) every rank advances its own field (seed = rank): weak scaling, no
 collective on the data path; the step time is the max over ranks.  `--impl reference` times the
@@ -233,7 +236,7 @@ def run_gpu(args, rank, world, local_rank, dist):
     flops = float(np.mean([_stiff_flops(s, ns, na) for s in stats]))
     achieved = flops / (stiff_ms / 1e3) / 1e12
     fp64_peak = chem.chem_measure_fp64_peak(reps=5)   # FMA chains on this GPU, outside the timed region
-    roof = {"kernel": "stiff_kernel", "bound": "alu", "pipe": "fp64", "achieved": achieved,
+    roof = {"kernel": "stiff_kernel" if ns <= 15 else "stiff_kernel_lg", "bound": "alu", "pipe": "fp64", "achieved": achieved,
             "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak,
             "traffic": _traffic() if args.config == 1 and args.edge == N_EDGE else None,
             "kernel_ms": stiff_ms, "bulk_kernel_ms": bulk_ms,
@@ -282,6 +285,7 @@ def run_gpu(args, rank, world, local_rank, dist):
                                        fp64_peak)
         line["config3"] = _config3_leg(args, chem, torch, dev, ctx, rank, world, dist, fp64_peak,
                                        gated="gated" in line)
+        line["config4"] = _config4_leg(args, chem, torch, dev, rank, world, dist, fp64_peak)
     if rank == 0 and world == 1 and args.cpu_baseline:
         # the 53-species oracle costs ~15 s per stiff cell per core: a smaller sample for config 4
         n_sample = args.cpu_sample if args.config == 1 else min(args.cpu_sample, 256)
@@ -310,9 +314,9 @@ def _stiff_flops(st, ns, na):
             + st["newton"] * f_newton(ns, na) + st["substeps"] * f_accept(ns, na))
 
 
-def _sampled_accuracy(mech, T, p, Y, hot, out_T, out_Y, dts, n_sample, seed):
-    """Error against the oracle on a stratified sample (half of it stiff cells): T, p, Y the inputs,
-    out_T, out_Y the GPU's results for the same cells, dts the cells' steps."""
+def _sampled_reference(mech, T, p, Y, hot, dts, n_sample, seed):
+    """The oracle's results on a stratified sample (half of it stiff cells) of the inputs T, p, Y
+    with steps dts: (sample indices, T, Y)."""
     import oracle
     idx = synth.stratified_sample(hot, n_sample, seed=seed, hot_frac=0.5)
     rho, e = oracle.state_from_TpY(mech, T[idx], p[idx], Y[:, idx])
@@ -322,6 +326,14 @@ def _sampled_accuracy(mech, T, p, Y, hot, out_T, out_Y, dts, n_sample, seed):
     for d in np.unique(dts[idx]):
         m = dts[idx] == d
         T_ref[m], _, Y_ref[:, m], _ = oracle.advance(mech, rho[m], e[m], T[idx][m], Y[:, idx][:, m], float(d))
+    return idx, T_ref, Y_ref
+
+
+def _sampled_accuracy(mech, T, p, Y, hot, out_T, out_Y, dts, n_sample, seed, ref=None):
+    """Error against the oracle on a stratified sample (half of it stiff cells): T, p, Y the inputs,
+    out_T, out_Y the GPU's results for the same cells, dts the cells' steps; ref a result of
+    _sampled_reference to compare against instead of a new sample."""
+    idx, T_ref, Y_ref = ref if ref is not None else _sampled_reference(mech, T, p, Y, hot, dts, n_sample, seed)
     Tg, Yg = out_T[idx].astype(np.float64), out_Y[:, idx].astype(np.float64)
     big = Y_ref >= 1e-6
     rel = np.where(big, np.abs(Yg - Y_ref) / np.maximum(Y_ref, 1e-300), 0.0)
@@ -478,6 +490,72 @@ def _config3_leg(args, chem, torch, dev, ctx1, rank, world, dist, fp64_peak, gat
                         "queued_cells": st_g["nqueued"],
                         "accuracy": _sampled_accuracy(mech, T, p, Y, hot, tT.cpu().numpy(), tY.cpu().numpy(), dts,
                                                       512, seed=rank)}
+    ctx.close()
+    return out
+
+
+def _config4_leg(args, chem, torch, dev, rank, world, dist, fp64_peak, edge=16, n_sample=32):
+    """Config 4 on a reduced sheet (2e x 2e x e cells, 4% reacting, e = 16: 16,384 cells) with the
+    53-species mechanism: the plain method (one warp per stiff cell) and the gated surrogate
+    (56 inputs, 54 outputs, trained here outside the timed region), each 1 warm-up + 2 timed
+    steps, both checked against the oracle on one stratified sample."""
+    mech, T, p, Y, hot = _field(seed=rank, edge=edge, config=4)
+    n, ns = T.size, mech["ns"]
+    ctx = chem.Context(mech, max_cells=max(n, 65536), rtol=args.rtol, atol=args.atol,
+                       flags=chem.CHEM_FLAG_TIMING | chem.CHEM_FLAG_ORDER_RATE)
+    tT, tp, tY = (torch.from_numpy(a).to(dev) for a in (T, p, Y))
+    rho, e = torch.empty_like(tT), torch.empty_like(tT)
+    ctx.state_from_TpY(tT, tp, tY, rho, e)
+    T0, Y0 = tT.clone(), tY.clone()
+    sub = torch.zeros(n, dtype=torch.int32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step(i):
+        tT.copy_(T0)
+        tY.copy_(Y0)
+        flush.fill_(i & 0xFF)
+        ctx.advance(tT, tp, tY, rho, e, DT, sub)
+        return ctx.status()
+
+    step(0)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    stats = [step(i) for i in range(2)]
+    ev1.record()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    for st in stats:
+        assert st["status"] == 0, st
+    ms = max_over_ranks(ev0.elapsed_time(ev1), dist) / 2
+    st = stats[-1]
+    na = active_species(mech)
+    stiff_ms = float(np.mean([x["stiff_ms"] for x in stats]))
+    achieved = _stiff_flops(st, ns, na) / (stiff_ms / 1e3) / 1e12
+    dts = np.full(n, DT)
+    ref = _sampled_reference(mech, T, p, Y, hot, dts, n_sample, seed=rank)
+    out = {"workload": f"reacting sheet {2 * edge}x{2 * edge}x{edge} ({n} cells, 4% reacting), hydrocarbon-shaped "
+                       f"mechanism {ns} species / {mech['nr']} reactions, dt = {DT:g} s, one warp per stiff cell",
+           "cells": n,
+           "plain": {"value": n * world / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "queued_cells": st["nqueued"],
+                     "substeps_per_stiff_cell": st["substeps"] / max(1, st["nqueued"]),
+                     "factorizations_per_attempt": st["factorizations"] / max(1, st["attempts"]),
+                     "roofline": {"kernel": "stiff_kernel_lg", "bound": "alu", "pipe": "fp64", "achieved": achieved,
+                                  "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak,
+                                  "kernel_ms": stiff_ms},
+                     "accuracy": _sampled_accuracy(mech, T, p, Y, hot, tT.cpu().numpy(), tY.cpu().numpy(), dts,
+                                                   n_sample, rank, ref=ref)},
+           "timing": "1 warm-up + 2 timed steps per leg, state restored and L2 flushed inside each step"}
+    if args.gated:
+        leg_args = argparse.Namespace(**{**vars(args), "steps": 2, "warmup": 1})
+        g = _gated_leg(leg_args, ctx, chem, torch, dev, mech, step_inputs=(tT, tp, tY, rho, e, sub, T0, Y0, flush),
+                       plain_ms=ms, n=n, world=world, dist=dist, rank=rank)
+        g["accuracy"] = _sampled_accuracy(mech, T, p, Y, hot, tT.cpu().numpy(), tY.cpu().numpy(), dts,
+                                          n_sample, rank, ref=ref)
+        out["gated"] = g
     ctx.close()
     return out
 
