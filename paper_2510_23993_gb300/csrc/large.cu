@@ -25,7 +25,9 @@
 namespace chem {
 namespace lg {
 
-constexpr int kStiffWarps = 5;   // cells in flight per CTA of the stiff kernel (shared memory bound)
+// cells in flight per CTA of the stiff kernel: as many warps as the shared memory holds (7 for
+// the 53-species tables), at most this many
+constexpr int kStiffWarpsMax = 8;
 constexpr int kBulkWarps = 8;    // cells in flight per CTA of the bulk kernel
 constexpr int kNewtMax = 6;
 constexpr double kNewtTol = 0.03;
@@ -93,7 +95,11 @@ __device__ __forceinline__ LView make_lview(const unsigned char* sm, const unsig
 __device__ __forceinline__ const float* gam_of(const LView& m, int reg, int r) { return m.gamg + (reg * m.nr + r) * 8; }
 __device__ __forceinline__ const float* hco_of(const LView& m, int reg, int r) { return m.hcog + (reg * m.nr + r) * 8; }
 
-// ---- per-warp scratch in shared memory
+// ---- per-warp scratch in shared memory.  J holds the rates of progress; in the stiff layout M
+// holds the FP64 iteration matrix and its factors, and while the Jacobian is built, the FP32
+// Jacobian in its first half and the per-reaction slopes behind it (the matrix is widened to FP64
+// in place afterwards).
+__host__ __device__ inline unsigned jac_slopes_offset(int ns) { return 4u * ((ns * ns + 3u) & ~3u); }
 struct ScratchLayout {
   unsigned C, lnC, dT, Mtb, piv, v, J, M, bytes;
 };
@@ -108,13 +114,14 @@ __host__ __device__ inline ScratchLayout scratch_layout(int ns, int nr, int ntb,
   l.piv = l.Mtb + 4 * mtb;
   l.v = (l.piv + 4 * nsp + 15) & ~15u;
   l.J = l.v + 8 * nsp;
-  unsigned jb = 8u * nr;   // rates of progress (FP64 at most)
-  if (stiff && 4u * ns * ns > jb) jb = 4u * ns * ns;
+  const unsigned jb = 8u * nr;   // rates of progress (FP64 at most)
   l.M = (l.J + jb + 15) & ~15u;
   unsigned mb = 0;
   if (stiff) {
     mb = 8u * ns * ns;
-    if (4u * 8 * nr > mb) mb = 4u * 8 * nr;   // Jacobian temporaries: 6 slopes, dq/dT, qf - qr
+    // FP32 Jacobian, then per reaction 6 slopes, dq/dT and qf - qr
+    const unsigned jac = jac_slopes_offset(ns) + 4u * 8 * nr;
+    if (jac > mb) mb = jac;
   }
   l.bytes = (l.M + mb + 127) & ~127u;
   return l;
@@ -321,8 +328,9 @@ __device__ __forceinline__ void warp_rates_safe(const LView& m, const Scratch& s
 }
 
 // Analytic FP32 Jacobian of dY/dt with T eliminated (dT/dY_j = -u_j / c_v), row k on lane k mod 32,
-// into s.J [NS][NS].  Per reaction the lanes store the slopes dq/dC_j of its (<= 6) species, dq/dT
-// and qf - qr (third-body rows) in the matrix area; each row then sums its reactions in order.
+// as FP32 [NS][NS] at the start of the matrix area (the factors of the previous matrix are
+// overwritten).  Per reaction the lanes store the slopes dq/dC_j of its (<= 6) species, dq/dT and
+// qf - qr (third-body rows) behind it; each row then sums its reactions in order.
 template <int NS>
 __device__ void warp_jacobian(const LView& m, const Scratch& s, float rho, float T, const float (&Yl)[2], float cvR) {
   const int lane = threadIdx.x & 31;
@@ -331,7 +339,8 @@ __device__ void warp_jacobian(const LView& m, const Scratch& s, float rho, float
   const float lnP0RT = m.lnP0R - lnT;
   const int reg = regime_of(T, m.T_lo, m.T_hi);
   const float T2 = T * T;
-  float* D = reinterpret_cast<float*>(s.M);   // [nr][6]
+  float* const Jf = reinterpret_cast<float*>(s.M);                                  // [NS][NS]
+  float* D = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(s.M) + jac_slopes_offset(NS));   // [nr][6]
   float* dqT = D + 6 * m.nr;                  // [nr]
   float* qd = dqT + m.nr;                     // [nr]
   for (int r = lane; r < m.nr; r += 32) {
@@ -379,7 +388,7 @@ __device__ void warp_jacobian(const LView& m, const Scratch& s, float rho, float
   for (int kk = 0; kk < 2; ++kk) {
     const int k = lane + 32 * kk;
     if (k < NS) {
-      float* Jk = s.J + k * NS;
+      float* Jk = Jf + k * NS;
 #pragma unroll 4
       for (int j = 0; j < NS; ++j) Jk[j] = 0.0f;
       float g = 0.0f;
@@ -411,16 +420,29 @@ __device__ void warp_jacobian(const LView& m, const Scratch& s, float rho, float
   __syncwarp();
 }
 
-// M = I - hh J (FP64, from the FP32 product as in stiff.cu)
+// M = I - hh J (FP64, from the FP32 product as in stiff.cu), widened in place from the FP32
+// Jacobian at the start of the same area.  Element idx is read at float offset idx and written at
+// float offsets 2 idx and 2 idx + 1.  The warp walks the matrix from its end in chunks of 32
+// elements: the chunk starting at c0 reads offsets [c0, c0 + 32) and then (after the __syncwarp)
+// writes [2 c0, 2 c0 + 64), which lies above everything the chunks below still read ([0, c0)) and
+// below what the chunks above wrote ([2 c0 + 64, ...)).
 template <int NS>
 __device__ __forceinline__ void warp_iteration_matrix(const Scratch& s, double hh) {
   const int lane = threadIdx.x & 31;
   const float mh = static_cast<float>(-hh);
-  for (int idx = lane; idx < NS * NS; idx += 32) {
-    const double v = static_cast<double>(mh * s.J[idx]);
-    s.M[idx] = (idx / NS == idx % NS) ? 1.0 + v : v;
+  const float* Jf = reinterpret_cast<const float*>(s.M);
+  constexpr int n2 = NS * NS;
+#pragma unroll 1
+  for (int c0 = ((n2 - 1) / 32) * 32; c0 >= 0; c0 -= 32) {
+    const int idx = c0 + lane;
+    const float j = idx < n2 ? Jf[idx] : 0.0f;
+    __syncwarp();
+    if (idx < n2) {
+      const double v = static_cast<double>(mh * j);
+      s.M[idx] = (idx / NS == idx % NS) ? 1.0 + v : v;
+    }
+    __syncwarp();
   }
-  __syncwarp();
 }
 
 // LU with partial pivoting by the warp (unit-lower L; U stored as D^-1 U, unit upper, with the
@@ -743,7 +765,7 @@ __global__ void __launch_bounds__(32 * kBulkWarps) bulk_kernel_lg(const AdvanceA
 // ------------------------------------------------------------------ stiff kernel (warp per cell)
 
 template <int NS>
-__global__ void __launch_bounds__(32 * kStiffWarps) stiff_kernel_lg(const AdvanceArgs<float> a) {
+__global__ void __launch_bounds__(32 * kStiffWarpsMax, 1) stiff_kernel_lg(const AdvanceArgs<float> a) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ uint64_t bar;
   if (!stage_to_smem(smem, a.blob, a.blob_bytes, &bar, &a.ws->status)) return;
@@ -985,8 +1007,22 @@ static unsigned pad128(unsigned b) { return (b + 127u) & ~127u; }
 size_t bulk_smem_bytes_lg(int ns, int nr, int ntb, unsigned prefix, int nbox) {
   return pad128(prefix) + box_smem_bytes(nbox) + lg::kBulkWarps * lg::scratch_layout(ns, nr, ntb, false).bytes;
 }
-size_t stiff_smem_bytes_lg(int ns, int nr, int ntb, unsigned prefix, int nbox) {
-  return pad128(prefix) + box_smem_bytes(nbox) + lg::kStiffWarps * lg::scratch_layout(ns, nr, ntb, true).bytes;
+size_t stiff_smem_bytes_lg(int ns, int nr, int ntb, unsigned prefix, int nbox, int warps) {
+  return pad128(prefix) + box_smem_bytes(nbox) + warps * lg::scratch_layout(ns, nr, ntb, true).bytes;
+}
+
+// Warps per CTA of the stiff kernel: as many per-warp scratch areas as fit next to the staged
+// tables in the device's opt-in shared memory per block (1 KB kept for the kernel's static shared
+// memory), between 1 and kStiffWarpsMax.
+static int stiff_warps_lg(int ns, int nr, int ntb, unsigned prefix, int nbox) {
+  int dev = 0, optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return 1;
+  const long long room = static_cast<long long>(optin) - 1024 -
+                         static_cast<long long>(stiff_smem_bytes_lg(ns, nr, ntb, prefix, nbox, 0));
+  const long long w = room / static_cast<long long>(lg::scratch_layout(ns, nr, ntb, true).bytes);
+  return w < 1 ? 1 : (w > lg::kStiffWarpsMax ? lg::kStiffWarpsMax : static_cast<int>(w));
 }
 
 int launch_bulk_lg(int ns, int nr, int ntb, const AdvanceArgs<float>& a, int grid, cudaStream_t s) {
@@ -1006,10 +1042,11 @@ int launch_bulk_lg(int ns, int nr, int ntb, const AdvanceArgs<float>& a, int gri
 int launch_stiff_lg(int ns, int nr, int ntb, const AdvanceArgs<float>& a, int grid, cudaStream_t s) {
 #define X(N)                                                                                     \
   if (ns == N) {                                                                                 \
-    const size_t smem = stiff_smem_bytes_lg(N, nr, ntb, a.blob_bytes, a.nbox);                   \
+    const int w = stiff_warps_lg(N, nr, ntb, a.blob_bytes, a.nbox);                              \
+    const size_t smem = stiff_smem_bytes_lg(N, nr, ntb, a.blob_bytes, a.nbox, w);                \
     cudaFuncSetAttribute(lg::stiff_kernel_lg<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
                          static_cast<int>(smem));                                                \
-    lg::stiff_kernel_lg<N><<<grid, 32 * lg::kStiffWarps, smem, s>>>(a);                          \
+    lg::stiff_kernel_lg<N><<<grid, 32 * w, smem, s>>>(a);                                        \
     return static_cast<int>(cudaGetLastError());                                                 \
   }
   CHEM_FOR_EACH_NS_LARGE(X)
@@ -1040,11 +1077,12 @@ int occupancy_lg(int ns, int nr, int ntb, unsigned prefix, bool stiff, int* bloc
 #define X(N)                                                                                          \
   if (ns == N) {                                                                                      \
     if (stiff) {                                                                                      \
-      const size_t smem = stiff_smem_bytes_lg(N, nr, ntb, prefix, 0);                                 \
+      const int w = stiff_warps_lg(N, nr, ntb, prefix, 0);                                            \
+      const size_t smem = stiff_smem_bytes_lg(N, nr, ntb, prefix, 0, w);                              \
       cudaFuncSetAttribute(lg::stiff_kernel_lg<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,       \
                            static_cast<int>(smem));                                                   \
       return static_cast<int>(cudaOccupancyMaxActiveBlocksPerMultiprocessor(                          \
-          blocks_per_sm, lg::stiff_kernel_lg<N>, 32 * lg::kStiffWarps, smem));                        \
+          blocks_per_sm, lg::stiff_kernel_lg<N>, 32 * w, smem));                                      \
     }                                                                                                 \
     const size_t smem = bulk_smem_bytes_lg(N, nr, ntb, prefix, 0);                                    \
     cudaFuncSetAttribute(lg::bulk_kernel_lg<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,          \
