@@ -170,16 +170,27 @@ __device__ __forceinline__ float wmax(float x) {
 
 // ---- temperature from internal energy: lanes reduce the FP64 mixture coefficients, every lane
 // runs the same scalar Newton iteration (bisection safeguard), as temperature_from_energy does.
+// The six sums over the warp: each of the first three butterfly levels halves the values a lane
+// carries (it keeps one half and hands its partner the other), so a lane does 4 + 2 + 1 + 1 + 1
+// FP64 additions instead of 6 x 5; lane l ends with the sum of value 4 b4 + 2 b3 + b2 (bits 4, 3
+// and 2 of l; values 6 and 7 are zero padding), and six broadcasts hand the sums to every lane.
+// Newton iterates stop at tol = 1e-5 T (their temperatures only feed the FP32 rates: the last
+// step leaves T within ~1e-11 of the root), accepted states at 3e-8 T.
+constexpr double kTeIterateTol = 1e-5;
+constexpr double kTeStateTol = 3e-8;
+
 template <int NS, typename Y_t>
 __device__ double warp_temperature(const LView& m, const Y_t (&y)[2], double e0, double T, bool* ok,
-                                   double* cv_out = nullptr) {
+                                   double* cv_out = nullptr, double tol = kTeStateTol) {
   const int lane = threadIdx.x & 31;
   const double eR = e0 * (1.0 / kR);
   double lo = kTbrLo, hi = kTbrHi;
   if (!(T > lo && T < hi)) T = 1000.0;
-  auto mixture = [&](int reg, double (&E)[6]) {
+  const bool b4 = (lane & 16) != 0, b3 = (lane & 8) != 0, b2 = (lane & 4) != 0;
+  auto mixture = [&](int reg, double (&E)[6], double (&D)[4]) {
+    double v[8];
 #pragma unroll
-    for (int j = 0; j < 6; ++j) E[j] = 0.0;
+    for (int j = 0; j < 8; ++j) v[j] = 0.0;
 #pragma unroll
     for (int kk = 0; kk < 2; ++kk) {
       const int k = lane + 32 * kk;
@@ -187,21 +198,35 @@ __device__ double warp_temperature(const LView& m, const Y_t (&y)[2], double e0,
         const double* c = m.mv.e64 + (reg * NS + k) * 8;
         const double yk = static_cast<double>(y[kk]);
 #pragma unroll
-        for (int j = 0; j < 6; ++j) E[j] = fma(yk, c[j], E[j]);
+        for (int j = 0; j < 6; ++j) v[j] = fma(yk, c[j], v[j]);
       }
     }
+    double w4[4], w2[2];
 #pragma unroll
-    for (int j = 0; j < 6; ++j) E[j] = wsum(E[j]);
+    for (int i = 0; i < 4; ++i)
+      w4[i] = (b4 ? v[4 + i] : v[i]) + __shfl_xor_sync(0xffffffffu, b4 ? v[i] : v[4 + i], 16);
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+      w2[i] = (b3 ? w4[2 + i] : w4[i]) + __shfl_xor_sync(0xffffffffu, b3 ? w4[i] : w4[2 + i], 8);
+    double w = (b2 ? w2[1] : w2[0]) + __shfl_xor_sync(0xffffffffu, b2 ? w2[0] : w2[1], 4);
+    w += __shfl_xor_sync(0xffffffffu, w, 2);
+    w += __shfl_xor_sync(0xffffffffu, w, 1);
+#pragma unroll
+    for (int j = 0; j < 6; ++j) E[j] = __shfl_sync(0xffffffffu, w, ((j & 4) << 2) | ((j & 2) << 2) | ((j & 1) << 2));
+    D[0] = 2.0 * E[2];
+    D[1] = 3.0 * E[3];
+    D[2] = 4.0 * E[4];
+    D[3] = 5.0 * E[5];
   };
   int reg = regime_of(static_cast<float>(T), m.T_lo, m.T_hi);
-  double E[6];
-  mixture(reg, E);
+  double E[6], D[4];   // D: the coefficients of de/dT, once per regime
+  mixture(reg, E, D);
   double cv = 0.0;
   bool conv = false;
 #pragma unroll 1
   for (int it = 0; it < 60; ++it) {
     const double f = fma(T, fma(T, fma(T, fma(T, fma(T, E[5], E[4]), E[3]), E[2]), E[1]), E[0]) - eR;
-    cv = fma(T, fma(T, fma(T, fma(T, 5.0 * E[5], 4.0 * E[4]), 3.0 * E[3]), 2.0 * E[2]), E[1]);
+    cv = fma(T, fma(T, fma(T, fma(T, D[3], D[2]), D[1]), D[0]), E[1]);
     if (f > 0.0) hi = T; else lo = T;
     double Tn = (cv > 0.0) ? T - f * static_cast<double>(__frcp_rn(static_cast<float>(cv))) : 0.5 * (lo + hi);
     if (!(Tn > lo && Tn < hi)) Tn = 0.5 * (lo + hi);
@@ -210,10 +235,10 @@ __device__ double warp_temperature(const LView& m, const Y_t (&y)[2], double e0,
     const int nreg = regime_of(static_cast<float>(T), m.T_lo, m.T_hi);
     if (nreg != reg) {
       reg = nreg;
-      mixture(reg, E);
+      mixture(reg, E, D);
       continue;
     }
-    if (fabs(dT) <= 3e-8 * T) {
+    if (fabs(dT) <= tol * T) {
       conv = true;
       break;
     }
@@ -551,7 +576,7 @@ __device__ bool warp_lu(const Scratch& s) {
 // sweeps: unit-lower L forward, then the unit upper D^-1 U backward on D^-1 y).
 template <int NS>
 __device__ void warp_solve(const Scratch& s, double (&b)[2]) {
-  static_assert(NS <= 64, "two entries per lane");
+  static_assert(NS > 32 && NS <= 64, "two entries per lane, the second half not empty");
   const int lane = threadIdx.x & 31;
   const double* M = s.M;
   double* v = s.v;
@@ -568,21 +593,34 @@ __device__ void warp_solve(const Scratch& s, double (&b)[2]) {
     x[kk] = k < NS ? v[s.piv[k]] : 0.0;
   }
   __syncwarp();
+  // Each sweep is split where one of the two halves (rows 0-31, rows 32-) has no row left to
+  // update, so that no FP64 instruction is issued with every lane predicated off (it would still
+  // take its turn on the FP64 pipe); the operations and their order are those of one sweep.
   const int i0 = lane, i1 = lane + 32;
 #pragma unroll 1
-  for (int j = 0; j < NS - 1; ++j) {
-    const double vj = __shfl_sync(0xffffffffu, j < 32 ? x[0] : x[1], j & 31);
+  for (int j = 0; j < 31; ++j) {   // rows below j in both halves (rows 32- are all below)
+    const double vj = __shfl_sync(0xffffffffu, x[0], j);
     if (i0 > j) x[0] = fma(-M[i0 * NS + j], vj, x[0]);
+    if (i1 < NS) x[1] = fma(-M[i1 * NS + j], vj, x[1]);
+  }
+#pragma unroll 1
+  for (int j = 31; j < NS - 1; ++j) {   // rows below j only in the second half
+    const double vj = __shfl_sync(0xffffffffu, j < 32 ? x[0] : x[1], j & 31);
     if (i1 > j && i1 < NS) x[1] = fma(-M[i1 * NS + j], vj, x[1]);
   }
   // back substitution with the unit upper factor D^-1 U on D^-1 y
   x[0] *= M[i0 * NS + i0];
   if (i1 < NS) x[1] *= M[i1 * NS + i1];
 #pragma unroll 1
-  for (int j = NS - 1; j >= 0; --j) {
-    const double vj = __shfl_sync(0xffffffffu, j < 32 ? x[0] : x[1], j & 31);
-    if (i0 < j) x[0] = fma(-M[i0 * NS + j], vj, x[0]);
+  for (int j = NS - 1; j >= 32; --j) {   // rows above j: all of the first half, part of the second
+    const double vj = __shfl_sync(0xffffffffu, x[1], j & 31);
+    x[0] = fma(-M[i0 * NS + j], vj, x[0]);
     if (i1 < j) x[1] = fma(-M[i1 * NS + j], vj, x[1]);
+  }
+#pragma unroll 1
+  for (int j = 31; j >= 1; --j) {   // rows above j only in the first half (none above row 0)
+    const double vj = __shfl_sync(0xffffffffu, x[0], j);
+    if (i0 < j) x[0] = fma(-M[i0 * NS + j], vj, x[0]);
   }
   b[0] = x[0];
   b[1] = i1 < NS ? x[1] : 0.0;
@@ -604,7 +642,7 @@ __device__ bool warp_stage_newton(const LView& m, const Scratch& s, const CellCt
   for (int it = 0; it < kNewtMax; ++it) {
     ++n_it;
     bool ok;
-    Tz = warp_temperature<NS>(m, z, c.e0, Tz, &ok);
+    Tz = warp_temperature<NS>(m, z, c.e0, Tz, &ok, nullptr, kTeIterateTol);
     if (!ok) return false;
     float Zf[2], F[2];
 #pragma unroll
