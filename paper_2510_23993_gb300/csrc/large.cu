@@ -450,7 +450,9 @@ __device__ void warp_jacobian(const LView& m, const Scratch& s, float rho, float
 // float offsets 2 idx and 2 idx + 1.  The warp walks the matrix from its end in chunks of 32
 // elements: the chunk starting at c0 reads offsets [c0, c0 + 32) and then (after the __syncwarp)
 // writes [2 c0, 2 c0 + 64), which lies above everything the chunks below still read ([0, c0)) and
-// below what the chunks above wrote ([2 c0 + 64, ...)).
+// below what the chunks above wrote ([2 c0 + 64, ...)).  The widening is the exact integer-pipe
+// conversion, and the identity is added to the diagonal afterwards (1 + v either way), so the
+// walk issues no FP64 instruction.
 template <int NS>
 __device__ __forceinline__ void warp_iteration_matrix(const Scratch& s, double hh) {
   const int lane = threadIdx.x & 31;
@@ -462,12 +464,11 @@ __device__ __forceinline__ void warp_iteration_matrix(const Scratch& s, double h
     const int idx = c0 + lane;
     const float j = idx < n2 ? Jf[idx] : 0.0f;
     __syncwarp();
-    if (idx < n2) {
-      const double v = static_cast<double>(mh * j);
-      s.M[idx] = (idx / NS == idx % NS) ? 1.0 + v : v;
-    }
+    if (idx < n2) s.M[idx] = f32_to_f64_exact(mh * j);
     __syncwarp();
   }
+  for (int i = lane; i < NS; i += 32) s.M[i * NS + i] += 1.0;
+  __syncwarp();
 }
 
 // LU with partial pivoting by the warp (unit-lower L; U stored as D^-1 U, unit upper, with the
@@ -571,12 +572,20 @@ __device__ bool warp_lu(const Scratch& s) {
 }
 
 // x = M^-1 b with the factors of warp_lu; b / x: this lane's entries lane and lane + 32.  The
-// permuted right-hand side is gathered through shared memory once; the substitutions then keep
-// x in registers (lane-owned entries) and broadcast each finished entry with a shuffle (column
-// sweeps: unit-lower L forward, then the unit upper D^-1 U backward on D^-1 y).
+// permuted right-hand side is gathered through shared memory; the substitutions keep x in
+// registers (two rows per lane) and broadcast each finished entry with a shuffle (column sweeps:
+// unit-lower L forward, then the unit upper D^-1 U backward on D^-1 y).  Each sweep lays its rows
+// over the lanes so that the rows still to update at column j fill as few warp instructions as
+// possible: forward, rows R.. (R = NS - 32) on the first register and rows 0..R-1 on the second,
+// so the first register's rows all lie below every column at which the second has any;
+// backward, rows 0-31 and 32-, so the first register's rows all lie above every column at which
+// the second has any.  Past that point a column takes one FP64 instruction instead of two, no
+// FP64 instruction runs with every lane predicated off (it would still take its turn on the
+// FP64 pipe), and every row takes its updates in the order of a plain column sweep.
 template <int NS>
 __device__ void warp_solve(const Scratch& s, double (&b)[2]) {
   static_assert(NS > 32 && NS <= 64, "two entries per lane, the second half not empty");
+  constexpr int R = NS - 32;
   const int lane = threadIdx.x & 31;
   const double* M = s.M;
   double* v = s.v;
@@ -586,40 +595,43 @@ __device__ void warp_solve(const Scratch& s, double (&b)[2]) {
     if (k < NS) v[k] = b[kk];
   }
   __syncwarp();
+  const int f0 = R + lane, f1 = lane;   // forward layout
   double x[2];
-#pragma unroll
-  for (int kk = 0; kk < 2; ++kk) {
-    const int k = lane + 32 * kk;
-    x[kk] = k < NS ? v[s.piv[k]] : 0.0;
-  }
+  x[0] = v[s.piv[f0]];
+  x[1] = f1 < R ? v[s.piv[f1]] : 0.0;
   __syncwarp();
-  // Each sweep is split where one of the two halves (rows 0-31, rows 32-) has no row left to
-  // update, so that no FP64 instruction is issued with every lane predicated off (it would still
-  // take its turn on the FP64 pipe); the operations and their order are those of one sweep.
+#pragma unroll 1
+  for (int j = 0; j < R - 1; ++j) {   // rows below j on both registers (all of the first)
+    const double vj = __shfl_sync(0xffffffffu, x[1], j);
+    x[0] = fma(-M[f0 * NS + j], vj, x[0]);
+    if (f1 > j && f1 < R) x[1] = fma(-M[f1 * NS + j], vj, x[1]);
+  }
+#pragma unroll 1
+  for (int j = R - 1; j < NS - 1; ++j) {   // rows below j only on the first register
+    const double src = j < R ? x[1] : x[0];
+    const double vj = __shfl_sync(0xffffffffu, src, j < R ? j : j - R);
+    if (f0 > j) x[0] = fma(-M[f0 * NS + j], vj, x[0]);
+  }
+  // to the backward layout through shared memory
+  v[f0] = x[0];
+  if (f1 < R) v[f1] = x[1];
+  __syncwarp();
   const int i0 = lane, i1 = lane + 32;
-#pragma unroll 1
-  for (int j = 0; j < 31; ++j) {   // rows below j in both halves (rows 32- are all below)
-    const double vj = __shfl_sync(0xffffffffu, x[0], j);
-    if (i0 > j) x[0] = fma(-M[i0 * NS + j], vj, x[0]);
-    if (i1 < NS) x[1] = fma(-M[i1 * NS + j], vj, x[1]);
-  }
-#pragma unroll 1
-  for (int j = 31; j < NS - 1; ++j) {   // rows below j only in the second half
-    const double vj = __shfl_sync(0xffffffffu, j < 32 ? x[0] : x[1], j & 31);
-    if (i1 > j && i1 < NS) x[1] = fma(-M[i1 * NS + j], vj, x[1]);
-  }
-  // back substitution with the unit upper factor D^-1 U on D^-1 y
+  x[0] = v[i0];
+  x[1] = i1 < NS ? v[i1] : 0.0;
+  __syncwarp();
   x[0] *= M[i0 * NS + i0];
   if (i1 < NS) x[1] *= M[i1 * NS + i1];
 #pragma unroll 1
-  for (int j = NS - 1; j >= 32; --j) {   // rows above j: all of the first half, part of the second
-    const double vj = __shfl_sync(0xffffffffu, x[1], j & 31);
+  for (int j = NS - 1; j > 32; --j) {   // rows above j on both registers (all of the first)
+    const double vj = __shfl_sync(0xffffffffu, x[1], j - 32);
     x[0] = fma(-M[i0 * NS + j], vj, x[0]);
     if (i1 < j) x[1] = fma(-M[i1 * NS + j], vj, x[1]);
   }
 #pragma unroll 1
-  for (int j = 31; j >= 1; --j) {   // rows above j only in the first half (none above row 0)
-    const double vj = __shfl_sync(0xffffffffu, x[0], j);
+  for (int j = 32; j >= 1; --j) {   // rows above j only on the first register (none above row 0)
+    const double src = j < 32 ? x[0] : x[1];
+    const double vj = __shfl_sync(0xffffffffu, src, j & 31);
     if (i0 < j) x[0] = fma(-M[i0 * NS + j], vj, x[0]);
   }
   b[0] = x[0];

@@ -64,19 +64,6 @@ struct Smem {
   __device__ double& vv(int k) const { return V[k * B + t]; }
 };
 
-// Exact FP32 -> FP64 conversion with integer operations.  On GB300 a conversion instruction
-// occupies the FP64 pipe (about as long as an FP64 FMA), and the FP64 pipe bounds this kernel; the
-// bit assembly runs on the integer pipe instead.  Zeros, subnormals, infinities and NaNs take the
-// conversion instruction.  The result is the same value as static_cast<double>.
-__device__ __forceinline__ double f32_to_f64_exact(float x) {
-  const unsigned u = __float_as_uint(x);
-  const unsigned e = (u >> 23) & 0xffu;
-  if (e == 0u || e == 0xffu) return static_cast<double>(x);
-  const unsigned m = u & 0x7fffffu;
-  const unsigned hi = (u & 0x80000000u) | ((e + 896u) << 20) | (m >> 3);   // 896 = 1023 - 127
-  return __hiloint2double(static_cast<int>(hi), static_cast<int>(m << 29));
-}
-
 // 1 / x for a pivot: the hardware approximation of the reciprocal (PTX rcp.approx.ftz.f64, relative
 // error below 2^-22 for normal x) refined by two Newton-Raphson steps r <- r + r (1 - x r), each of
 // which squares the relative error, to within an ulp or two of the FP64 reciprocal.  Four FP64
