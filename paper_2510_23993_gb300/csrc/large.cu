@@ -475,6 +475,9 @@ __device__ __forceinline__ void warp_iteration_matrix(const Scratch& s, double h
 // reciprocals D^-1 of its pivots on the diagonal; s.piv holds the composite row permutation: row
 // k of the factors is row s.piv[k] of the original matrix).  Scaling U's rows once here lets every
 // solve apply D^-1 to its right-hand side in one step instead of a one-lane multiply per row.
+// Only the leading na x na block is factored: the trailing inert species (no reaction changes
+// them) have identity rows, zero residuals and zero updates, so their rows and columns take no
+// part in the solves, and their rows never win a pivot search before column na.
 // Returns false (warp-uniform) for a singular matrix.
 // |x| as an unsigned integer: for finite values it orders like |x|, so the pivot search compares
 // integers instead of FP64 values and picks the same pivot
@@ -495,17 +498,17 @@ __device__ __forceinline__ double pivot_rcp(double x) {
 }
 
 template <int NS>
-__device__ bool warp_lu(const Scratch& s) {
+__device__ bool warp_lu(const Scratch& s, int na) {
   const int lane = threadIdx.x & 31;
   double* M = s.M;
   for (int i = lane; i < NS; i += 32) s.piv[i] = i;
   __syncwarp();
 #pragma unroll 1
-  for (int k = 0; k < NS; ++k) {
+  for (int k = 0; k < na; ++k) {
     // the pivot search on integer keys of |M_ik| (integer pipe instead of FP64 compares)
     unsigned long long best = 0ull;
     int p = NS;
-    for (int i = k + lane; i < NS; i += 32) {
+    for (int i = k + lane; i < na; i += 32) {
       const unsigned long long v = abs_key64(M[i * NS + k]);
       if (p == NS || v > best) {
         best = v;
@@ -529,7 +532,7 @@ __device__ bool warp_lu(const Scratch& s) {
         s.piv[k] = s.piv[p];
         s.piv[p] = t;
       }
-      for (int c = lane; c < NS; c += 32) {
+      for (int c = lane; c < na; c += 32) {
         const double t = M[k * NS + c];
         M[k * NS + c] = M[p * NS + c];
         M[p * NS + c] = t;
@@ -537,13 +540,13 @@ __device__ bool warp_lu(const Scratch& s) {
     }
     __syncwarp();
     const double inv = pivot_rcp(M[k * NS + k]);
-    for (int i = k + 1 + lane; i < NS; i += 32) M[i * NS + k] *= inv;
+    for (int i = k + 1 + lane; i < na; i += 32) M[i * NS + k] *= inv;
     __syncwarp();
     // rank-1 update of the trailing m x m block, spread over the lanes element by element
     // (row-major order), so that all 32 lanes work until the block is smaller than the warp;
     // every element takes the same single FMA as in a column-per-lane sweep
-    if (k < NS - 1) {
-      const int m = NS - 1 - k;
+    if (k < na - 1) {
+      const int m = na - 1 - k;
       const int q = 32 / m, r = 32 - q * m;   // a stride of 32 elements: q rows and r columns
       int ii = lane / m, cc = lane - (lane / m) * m;
       for (int e = lane; e < m * m; e += 32) {
@@ -563,40 +566,60 @@ __device__ bool warp_lu(const Scratch& s) {
   }
   // U -> D^-1 U: row i of the strict upper triangle times its pivot's reciprocal
 #pragma unroll 1
-  for (int i = 0; i < NS - 1; ++i) {
+  for (int i = 0; i < na - 1; ++i) {
     const double d = M[i * NS + i];
-    for (int c = i + 1 + lane; c < NS; c += 32) M[i * NS + c] *= d;
+    for (int c = i + 1 + lane; c < na; c += 32) M[i * NS + c] *= d;
   }
   __syncwarp();
   return true;
 }
 
-// x = M^-1 b with the factors of warp_lu; b / x: this lane's entries lane and lane + 32.  The
-// permuted right-hand side is gathered through shared memory; the substitutions keep x in
-// registers (two rows per lane) and broadcast each finished entry with a shuffle (column sweeps:
-// unit-lower L forward, then the unit upper D^-1 U backward on D^-1 y).  Each sweep lays its rows
-// over the lanes so that the rows still to update at column j fill as few warp instructions as
-// possible: forward, rows R.. (R = NS - 32) on the first register and rows 0..R-1 on the second,
-// so the first register's rows all lie below every column at which the second has any;
-// backward, rows 0-31 and 32-, so the first register's rows all lie above every column at which
-// the second has any.  Past that point a column takes one FP64 instruction instead of two, no
-// FP64 instruction runs with every lane predicated off (it would still take its turn on the
-// FP64 pipe), and every row takes its updates in the order of a plain column sweep.
+// x = M^-1 b with the factors of warp_lu; b / x: this lane's entries lane and lane + 32 (the
+// entries of the inert species na.. come back zero).  The permuted right-hand side is gathered
+// through shared memory; the substitutions keep x in registers (up to two rows per lane) and
+// broadcast each finished entry with a shuffle (column sweeps: unit-lower L forward, then the
+// unit upper D^-1 U backward on D^-1 y).  With na > 32 each sweep lays its rows over the lanes so
+// that the rows still to update at column j fill as few warp instructions as possible: forward,
+// rows R.. (R = na - 32) on the first register and rows 0..R-1 on the second, so the first
+// register's rows all lie below every column at which the second has any; backward, rows 0-31
+// and 32-, so the first register's rows all lie above every column at which the second has any.
+// Past that point a column takes one FP64 instruction instead of two, no FP64 instruction runs
+// with every lane predicated off (it would still take its turn on the FP64 pipe), and every row
+// takes its updates in the order of a plain column sweep.
 template <int NS>
-__device__ void warp_solve(const Scratch& s, double (&b)[2]) {
-  static_assert(NS > 32 && NS <= 64, "two entries per lane, the second half not empty");
-  constexpr int R = NS - 32;
+__device__ void warp_solve(const Scratch& s, double (&b)[2], int na) {
+  static_assert(NS > 32 && NS <= 64, "two entries per lane");
   const int lane = threadIdx.x & 31;
   const double* M = s.M;
   double* v = s.v;
 #pragma unroll
   for (int kk = 0; kk < 2; ++kk) {
     const int k = lane + 32 * kk;
-    if (k < NS) v[k] = b[kk];
+    if (k < na) v[k] = b[kk];
   }
   __syncwarp();
-  const int f0 = R + lane, f1 = lane;   // forward layout
+  const int i0 = lane, i1 = lane + 32;
   double x[2];
+  if (na <= 32) {   // one row per lane
+    x[0] = i0 < na ? v[s.piv[i0]] : 0.0;
+    __syncwarp();
+#pragma unroll 1
+    for (int j = 0; j < na - 1; ++j) {
+      const double vj = __shfl_sync(0xffffffffu, x[0], j);
+      if (i0 > j && i0 < na) x[0] = fma(-M[i0 * NS + j], vj, x[0]);
+    }
+    if (i0 < na) x[0] *= M[i0 * NS + i0];
+#pragma unroll 1
+    for (int j = na - 1; j >= 1; --j) {
+      const double vj = __shfl_sync(0xffffffffu, x[0], j);
+      if (i0 < j) x[0] = fma(-M[i0 * NS + j], vj, x[0]);
+    }
+    b[0] = i0 < na ? x[0] : 0.0;
+    b[1] = 0.0;
+    return;
+  }
+  const int R = na - 32;
+  const int f0 = R + lane, f1 = lane;   // forward layout
   x[0] = v[s.piv[f0]];
   x[1] = f1 < R ? v[s.piv[f1]] : 0.0;
   __syncwarp();
@@ -607,7 +630,7 @@ __device__ void warp_solve(const Scratch& s, double (&b)[2]) {
     if (f1 > j && f1 < R) x[1] = fma(-M[f1 * NS + j], vj, x[1]);
   }
 #pragma unroll 1
-  for (int j = R - 1; j < NS - 1; ++j) {   // rows below j only on the first register
+  for (int j = R - 1; j < na - 1; ++j) {   // rows below j only on the first register
     const double src = j < R ? x[1] : x[0];
     const double vj = __shfl_sync(0xffffffffu, src, j < R ? j : j - R);
     if (f0 > j) x[0] = fma(-M[f0 * NS + j], vj, x[0]);
@@ -616,14 +639,13 @@ __device__ void warp_solve(const Scratch& s, double (&b)[2]) {
   v[f0] = x[0];
   if (f1 < R) v[f1] = x[1];
   __syncwarp();
-  const int i0 = lane, i1 = lane + 32;
   x[0] = v[i0];
-  x[1] = i1 < NS ? v[i1] : 0.0;
+  x[1] = i1 < na ? v[i1] : 0.0;
   __syncwarp();
   x[0] *= M[i0 * NS + i0];
-  if (i1 < NS) x[1] *= M[i1 * NS + i1];
+  if (i1 < na) x[1] *= M[i1 * NS + i1];
 #pragma unroll 1
-  for (int j = NS - 1; j > 32; --j) {   // rows above j on both registers (all of the first)
+  for (int j = na - 1; j > 32; --j) {   // rows above j on both registers (all of the first)
     const double vj = __shfl_sync(0xffffffffu, x[1], j - 32);
     x[0] = fma(-M[i0 * NS + j], vj, x[0]);
     if (i1 < j) x[1] = fma(-M[i1 * NS + j], vj, x[1]);
@@ -635,7 +657,7 @@ __device__ void warp_solve(const Scratch& s, double (&b)[2]) {
     if (i0 < j) x[0] = fma(-M[i0 * NS + j], vj, x[0]);
   }
   b[0] = x[0];
-  b[1] = i1 < NS ? x[1] : 0.0;
+  b[1] = i1 < na ? x[1] : 0.0;
 }
 
 struct CellCtx {
@@ -665,7 +687,7 @@ __device__ bool warp_stage_newton(const LView& m, const Scratch& s, const CellCt
 #pragma unroll
     for (int kk = 0; kk < 2; ++kk)
       b[kk] = (lane + 32 * kk < NS) ? (yb[kk] - z[kk]) + static_cast<double>(mhh * F[kk]) : 0.0;
-    warp_solve<NS>(s, b);
+    warp_solve<NS>(s, b, m.mv.nact);
     float ss = 0.0f;
 #pragma unroll
     for (int kk = 0; kk < 2; ++kk) {
@@ -889,7 +911,7 @@ __global__ void __launch_bounds__(32 * kStiffWarpsMax, 1) stiff_kernel_lg(const 
         for (int kk = 0; kk < 2; ++kk) Yf[kk] = static_cast<float>(y[kk]);
         warp_jacobian<NS>(m, s, c.rho, static_cast<float>(Tc), Yf, cvR);
         warp_iteration_matrix<NS>(s, gh);
-        conv = warp_lu<NS>(s);
+        conv = warp_lu<NS>(s, m.mv.nact);
         ++c_lu;
         lu_valid = conv;
         h_lu = h;
@@ -932,7 +954,7 @@ __global__ void __launch_bounds__(32 * kStiffWarpsMax, 1) stiff_kernel_lg(const 
           const double hk3 = (z[kk] - base[kk]) * (1.0 / kG);
           er[kk] = (kB1 - kBh1) * hk1[kk] + (kB2 - kBh2) * hk2[kk] + kG * hk3;
         }
-        warp_solve<NS>(s, er);
+        warp_solve<NS>(s, er, m.mv.nact);
         // the weighted error norm is a step-size control quantity: FP32
         float errl = 0.0f;
 #pragma unroll
