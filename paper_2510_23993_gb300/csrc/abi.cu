@@ -22,6 +22,7 @@ using namespace chem;
 struct chem_ctx {
   int dev = 0, sms = 0;
   int ns = 0, nr = 0, ntb = 0;
+  int nact = 0;                    // species before the trailing inert ones (packed header)
   unsigned char* blob = nullptr;   // device, 16-byte aligned
   unsigned blob_bytes = 0;
   chem_params prm{};
@@ -190,7 +191,7 @@ int advance_impl(chem_ctx* ctx, S* T, S* p, S* Y, int64_t ld, const S* rho, cons
         r1 = launch_bulk_lg(ctx->ns, ctx->nr, ctx->ntb, a, lgrid, st);
         if (!r1 && order) r1 = launch_order_queue(ctx->ws, ctx->queue, ctx->qkey, ctx->queue2, n, st);
         if (timed && !r1) cudaEventRecord(ctx->ev[1], st);
-        r2 = r1 ? r1 : launch_stiff_lg(ctx->ns, ctx->nr, ctx->ntb, b, ctx->stiff_grid, st);
+        r2 = r1 ? r1 : launch_stiff_lg(ctx->ns, ctx->nact, ctx->nr, ctx->ntb, b, ctx->stiff_grid, st);
       } else {
         return CHEM_EUNSUPPORTED;
       }
@@ -240,13 +241,13 @@ void ctx_set_sched(chem_ctx* c, int stiff_block, int probe_att, int round_att) {
 }
 int occupancy_bulk(const chem_ctx* c) {
   int b = 0;
-  const int r = c->large ? occupancy_lg(c->ns, c->nr, c->ntb, c->blob_bytes, false, &b)
+  const int r = c->large ? occupancy_lg(c->ns, c->nact, c->nr, c->ntb, c->blob_bytes, false, &b)
                          : bulk_occupancy(c->ns, false, c->blob_bytes, &b);
   return (r != 0 || b < 1) ? 1 : b;
 }
 int occupancy_stiff(const chem_ctx* c) {
   int b = 0;
-  const int r = c->large ? occupancy_lg(c->ns, c->nr, c->ntb, c->blob_bytes, true, &b)
+  const int r = c->large ? occupancy_lg(c->ns, c->nact, c->nr, c->ntb, c->blob_bytes, true, &b)
                          : stiff_occupancy(c->ns, c->blob_bytes, c->stiff_block, &b);
   return (r != 0 || b < 1) ? 1 : b;
 }
@@ -319,6 +320,10 @@ int chem_init(const chem_mechanism* mech, const chem_params* params, int64_t max
   const unsigned blob_total = static_cast<unsigned>(blob.size());
   // the staged part: the whole dense blob, or the large layout's prefix (its tail stays global)
   c->blob_bytes = reinterpret_cast<const MechHdr*>(blob.data())->prefix;
+  {
+    const MechHdr* hdr = reinterpret_cast<const MechHdr*>(blob.data());
+    c->nact = hdr->nact > 0 ? hdr->nact : hdr->ns;   // as the kernels' view of the header
+  }
   if ((rc = cuda_fail(cudaGetDevice(&c->dev), "cudaGetDevice"))) return fail(rc);
   if ((rc = cuda_fail(cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->dev), "attr"))) return fail(rc);
   if (cudaMalloc(&c->blob, blob_total) != cudaSuccess) return fail(CHEM_ENOMEM);
@@ -589,7 +594,7 @@ int chem_advance_boxes(chem_ctx* ctx, void* stream) {
       const int lgrid = static_cast<int>(wb < ctx->bulk_grid ? (wb < 1 ? 1 : wb) : ctx->bulk_grid);
       r1 = launch_bulk_lg(ctx->ns, ctx->nr, ctx->ntb, a, lgrid, st);
       if (!r1 && order) r1 = launch_order_queue(ctx->ws, ctx->queue, ctx->qkey, ctx->queue2, n, st);
-      r2 = r1 ? r1 : launch_stiff_lg(ctx->ns, ctx->nr, ctx->ntb, b, ctx->stiff_grid, st);
+      r2 = r1 ? r1 : launch_stiff_lg(ctx->ns, ctx->nact, ctx->nr, ctx->ntb, b, ctx->stiff_grid, st);
     } else {
       r1 = launch_bulk_f32(ctx->ns, a, bgrid, st);
       if (!r1 && order) r1 = launch_order_queue(ctx->ws, ctx->queue, ctx->qkey, ctx->queue2, n, st);

@@ -184,6 +184,15 @@ int launch_order_queue(Workspace* ws, const int* queue, const unsigned char* qke
   return static_cast<int>(cudaGetLastError());
 }
 
+// The thermo view of a blob whose first `bytes` are staged in shared memory: the large layout
+// keeps its FP64 thermo coefficients in the global tail, read from there through L1.
+__device__ __forceinline__ MechView thermo_view(const unsigned char* smem, const unsigned char* blob, unsigned bytes) {
+  MechView m = make_view(smem);
+  const MechHdr* h = reinterpret_cast<const MechHdr*>(smem);
+  if (static_cast<unsigned>(h->off_e64) >= bytes) m.e64 = reinterpret_cast<const double*>(blob + h->off_e64);
+  return m;
+}
+
 // rho = p / (R T sum Y/W), e = R * e/R(T) (FP64)
 template <int NS, typename S>
 __global__ void __launch_bounds__(kBulkBlock) state_kernel(const unsigned char* blob, unsigned bytes, const S* T,
@@ -192,7 +201,7 @@ __global__ void __launch_bounds__(kBulkBlock) state_kernel(const unsigned char* 
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ uint64_t bar;
   if (!stage_to_smem(smem, blob, bytes, &bar, status)) return;
-  const MechView m = make_view(smem);
+  const MechView m = thermo_view(smem, blob, bytes);
   for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
        i += static_cast<long long>(gridDim.x) * blockDim.x) {
     const double t = static_cast<double>(T[i]);
@@ -217,7 +226,7 @@ __global__ void __launch_bounds__(kBulkBlock) temperature_kernel(const unsigned 
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ uint64_t bar;
   if (!stage_to_smem(smem, blob, bytes, &bar, status)) return;
-  const MechView m = make_view(smem);
+  const MechView m = thermo_view(smem, blob, bytes);
   for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
        i += static_cast<long long>(gridDim.x) * blockDim.x) {
     float y[NS];
@@ -254,7 +263,8 @@ __global__ void __launch_bounds__(kBulkBlock) rates_kernel(const unsigned char* 
 
 #define CHEM_FOR_EACH_NS(X) X(9)
 // species counts of the thread-per-cell thermo helpers (state_kernel, temperature_kernel): also
-// the large mechanisms, whose staged table prefix carries the same thermo layout
+// the large mechanisms, whose blobs carry the same thermo layout (their FP64 coefficients in the
+// global tail)
 #define CHEM_FOR_EACH_NS_THERMO(X) X(9) X(53)
 
 size_t bulk_smem_bytes(unsigned blob_bytes, int nbox) {

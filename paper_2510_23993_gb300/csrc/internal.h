@@ -44,11 +44,11 @@ int launch_explicit(int ns, const AdvanceArgs<float>& a, double* tcell, int mode
 // large mechanisms (large.cu): one warp per cell, sparse stoichiometry
 bool compiled_large(int ns);
 int launch_bulk_lg(int ns, int nr, int ntb, const AdvanceArgs<float>& a, int grid, cudaStream_t s);
-int launch_stiff_lg(int ns, int nr, int ntb, const AdvanceArgs<float>& a, int grid, cudaStream_t s);
+int launch_stiff_lg(int ns, int na, int nr, int ntb, const AdvanceArgs<float>& a, int grid, cudaStream_t s);
 int launch_rates_lg(int ns, int nr, int ntb, const unsigned char* blob, unsigned bytes, const float* rho,
                     const float* T, const float* Y, long long ld, long long n, float* dYdt, int* status,
                     cudaStream_t s);
-int occupancy_lg(int ns, int nr, int ntb, unsigned prefix, bool stiff, int* blocks_per_sm);
+int occupancy_lg(int ns, int na, int nr, int ntb, unsigned prefix, bool stiff, int* blocks_per_sm);
 
 // large mechanisms, rates with the stoichiometric contractions on the tensor cores (rates_tc.cu)
 bool rates_tc_supported(int ns, int ntb);

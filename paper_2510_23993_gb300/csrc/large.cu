@@ -58,12 +58,12 @@ struct LView {
   const float* invW;
   const float* eff;     // [ntb][nsp]
   const float* hsp;     // [3][ns][8] species h/RT coefficients
-  const int2* sto;      // [nr] packed reactants, products
+  const int2* sto;      // [nr] packed reactants, products (global memory)
   const int* cptr;      // [ns + 1]
   const int* cent;      // [nnz] reaction | dnu << 16
   const float* gamg;    // [3][nr][8] all regimes (global memory)
   const float* hcog;
-  MechView mv;          // e64 and the fit range for the temperature inversion
+  MechView mv;          // e64 (global memory) and the fit range for the temperature inversion
 };
 
 __device__ __forceinline__ LView make_lview(const unsigned char* sm, const unsigned char* gl) {
@@ -82,12 +82,13 @@ __device__ __forceinline__ LView make_lview(const unsigned char* sm, const unsig
   v.invW = reinterpret_cast<const float*>(sm + h->off_invW);
   v.eff = reinterpret_cast<const float*>(sm + h->off_eff);
   v.hsp = reinterpret_cast<const float*>(sm + h->off_hsp);
-  v.sto = reinterpret_cast<const int2*>(sm + h->off_sto);
+  v.sto = reinterpret_cast<const int2*>(gl + h->off_sto);
   v.cptr = reinterpret_cast<const int*>(sm + h->off_cptr);
   v.cent = reinterpret_cast<const int*>(sm + h->off_cent);
   v.gamg = reinterpret_cast<const float*>(gl + h->off_gamg);
   v.hcog = reinterpret_cast<const float*>(gl + h->off_hcog);
   v.mv = make_view(sm);
+  v.mv.e64 = reinterpret_cast<const double*>(gl + h->off_e64);
   return v;
 }
 
@@ -103,7 +104,7 @@ __host__ __device__ inline unsigned jac_slopes_offset(int ns) { return 4u * ((ns
 struct ScratchLayout {
   unsigned C, lnC, dT, Mtb, piv, v, J, M, bytes;
 };
-__host__ __device__ inline ScratchLayout scratch_layout(int ns, int nr, int ntb, bool stiff) {
+__host__ __device__ inline ScratchLayout scratch_layout(int ns, int nr, int ntb, bool stiff, int na = 0) {
   ScratchLayout l;
   const unsigned nsp = (ns + 3) & ~3;
   const unsigned mtb = ((ntb > 0 ? ntb : 1) + 3) & ~3;
@@ -118,9 +119,11 @@ __host__ __device__ inline ScratchLayout scratch_layout(int ns, int nr, int ntb,
   l.M = (l.J + jb + 15) & ~15u;
   unsigned mb = 0;
   if (stiff) {
-    mb = 8u * ns * ns;
+    // the leading na x na block (na: species before the trailing inert ones) with row stride na
+    const int nj = na > 0 ? na : ns;
+    mb = 8u * nj * nj;
     // FP32 Jacobian, then per reaction 6 slopes, dq/dT and qf - qr
-    const unsigned jac = jac_slopes_offset(ns) + 4u * 8 * nr;
+    const unsigned jac = jac_slopes_offset(nj) + 4u * 8 * nr;
     if (jac > mb) mb = jac;
   }
   l.bytes = (l.M + mb + 127) & ~127u;
@@ -353,8 +356,8 @@ __device__ __forceinline__ void warp_rates_safe(const LView& m, const Scratch& s
 }
 
 // Analytic FP32 Jacobian of dY/dt with T eliminated (dT/dY_j = -u_j / c_v), row k on lane k mod 32,
-// as FP32 [NS][NS] at the start of the matrix area (the factors of the previous matrix are
-// overwritten).  Per reaction the lanes store the slopes dq/dC_j of its (<= 6) species, dq/dT and
+// its leading na x na block (the rows and columns of the non-inert species; row stride na) as FP32
+// at the start of the matrix area (the factors of the previous matrix are overwritten).  Per reaction the lanes store the slopes dq/dC_j of its (<= 6) species, dq/dT and
 // qf - qr (third-body rows) behind it; each row then sums its reactions in order.
 template <int NS>
 __device__ void warp_jacobian(const LView& m, const Scratch& s, float rho, float T, const float (&Yl)[2], float cvR) {
@@ -365,7 +368,8 @@ __device__ void warp_jacobian(const LView& m, const Scratch& s, float rho, float
   const int reg = regime_of(T, m.T_lo, m.T_hi);
   const float T2 = T * T;
   float* const Jf = reinterpret_cast<float*>(s.M);                                  // [NS][NS]
-  float* D = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(s.M) + jac_slopes_offset(NS));   // [nr][6]
+  const int na = m.mv.nact;
+  float* D = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(s.M) + jac_slopes_offset(na));   // [nr][6]
   float* dqT = D + 6 * m.nr;                  // [nr]
   float* qd = dqT + m.nr;                     // [nr]
   for (int r = lane; r < m.nr; r += 32) {
@@ -412,10 +416,10 @@ __device__ void warp_jacobian(const LView& m, const Scratch& s, float rho, float
 #pragma unroll
   for (int kk = 0; kk < 2; ++kk) {
     const int k = lane + 32 * kk;
-    if (k < NS) {
-      float* Jk = Jf + k * NS;
+    if (k < na) {
+      float* Jk = Jf + k * na;
 #pragma unroll 4
-      for (int j = 0; j < NS; ++j) Jk[j] = 0.0f;
+      for (int j = 0; j < na; ++j) Jk[j] = 0.0f;
       float g = 0.0f;
       for (int e = m.cptr[k]; e < m.cptr[k + 1]; ++e) {
         const int ent = m.cent[e];
@@ -424,22 +428,23 @@ __device__ void warp_jacobian(const LView& m, const Scratch& s, float rho, float
         g = fmaf(dn, dqT[r], g);
         const int2 st = m.sto[r];
 #pragma unroll
-        for (int j = 0; j < 3; ++j) {
-          if (sto_c(st.x, j)) Jk[sto_sp(st.x, j)] += dn * D[r * 6 + j];
-          if (sto_c(st.y, j)) Jk[sto_sp(st.y, j)] += dn * D[r * 6 + 3 + j];
+        for (int j = 0; j < 3; ++j) {   // (an inert species' column is not kept)
+          const int sf = sto_sp(st.x, j), sb = sto_sp(st.y, j);
+          if (sto_c(st.x, j) && sf < na) Jk[sf] += dn * D[r * 6 + j];
+          if (sto_c(st.y, j) && sb < na) Jk[sb] += dn * D[r * 6 + 3 + j];
         }
         const int tb = (m.rinfo[r] >> 8) - 1;
         if (tb >= 0) {   // d[M]/dC_j = eff_j: a dense row contribution
           const float dq = dn * qd[r];
           const float* ef = m.eff + tb * m.nsp;
 #pragma unroll 4
-          for (int j = 0; j < NS; ++j) Jk[j] = fmaf(dq, ef[j], Jk[j]);
+          for (int j = 0; j < na; ++j) Jk[j] = fmaf(dq, ef[j], Jk[j]);
         }
       }
       const float Wk = m.W[k];
       const float gk = g * Wk * irho;
 #pragma unroll 4
-      for (int j = 0; j < NS; ++j) Jk[j] = Jk[j] * Wk * m.invW[j] + gk * s.dT[j];
+      for (int j = 0; j < na; ++j) Jk[j] = Jk[j] * Wk * m.invW[j] + gk * s.dT[j];
     }
   }
   __syncwarp();
@@ -454,11 +459,11 @@ __device__ void warp_jacobian(const LView& m, const Scratch& s, float rho, float
 // conversion, and the identity is added to the diagonal afterwards (1 + v either way), so the
 // walk issues no FP64 instruction.
 template <int NS>
-__device__ __forceinline__ void warp_iteration_matrix(const Scratch& s, double hh) {
+__device__ __forceinline__ void warp_iteration_matrix(const Scratch& s, double hh, int na) {
   const int lane = threadIdx.x & 31;
   const float mh = static_cast<float>(-hh);
   const float* Jf = reinterpret_cast<const float*>(s.M);
-  constexpr int n2 = NS * NS;
+  const int n2 = na * na;
 #pragma unroll 1
   for (int c0 = ((n2 - 1) / 32) * 32; c0 >= 0; c0 -= 32) {
     const int idx = c0 + lane;
@@ -467,7 +472,7 @@ __device__ __forceinline__ void warp_iteration_matrix(const Scratch& s, double h
     if (idx < n2) s.M[idx] = f32_to_f64_exact(mh * j);
     __syncwarp();
   }
-  for (int i = lane; i < NS; i += 32) s.M[i * NS + i] += 1.0;
+  for (int i = lane; i < na; i += 32) s.M[i * na + i] += 1.0;
   __syncwarp();
 }
 
@@ -509,7 +514,7 @@ __device__ bool warp_lu(const Scratch& s, int na) {
     unsigned long long best = 0ull;
     int p = NS;
     for (int i = k + lane; i < na; i += 32) {
-      const unsigned long long v = abs_key64(M[i * NS + k]);
+      const unsigned long long v = abs_key64(M[i * na + k]);
       if (p == NS || v > best) {
         best = v;
         p = i;
@@ -533,14 +538,14 @@ __device__ bool warp_lu(const Scratch& s, int na) {
         s.piv[p] = t;
       }
       for (int c = lane; c < na; c += 32) {
-        const double t = M[k * NS + c];
-        M[k * NS + c] = M[p * NS + c];
-        M[p * NS + c] = t;
+        const double t = M[k * na + c];
+        M[k * na + c] = M[p * na + c];
+        M[p * na + c] = t;
       }
     }
     __syncwarp();
-    const double inv = pivot_rcp(M[k * NS + k]);
-    for (int i = k + 1 + lane; i < na; i += 32) M[i * NS + k] *= inv;
+    const double inv = pivot_rcp(M[k * na + k]);
+    for (int i = k + 1 + lane; i < na; i += 32) M[i * na + k] *= inv;
     __syncwarp();
     // rank-1 update of the trailing m x m block, spread over the lanes element by element
     // (row-major order), so that all 32 lanes work until the block is smaller than the warp;
@@ -551,7 +556,7 @@ __device__ bool warp_lu(const Scratch& s, int na) {
       int ii = lane / m, cc = lane - (lane / m) * m;
       for (int e = lane; e < m * m; e += 32) {
         const int i = k + 1 + ii, c = k + 1 + cc;
-        M[i * NS + c] = fma(-M[i * NS + k], M[k * NS + c], M[i * NS + c]);
+        M[i * na + c] = fma(-M[i * na + k], M[k * na + c], M[i * na + c]);
         ii += q;
         cc += r;
         if (cc >= m) {
@@ -561,14 +566,14 @@ __device__ bool warp_lu(const Scratch& s, int na) {
       }
     }
     __syncwarp();
-    if (lane == 0) M[k * NS + k] = inv;
+    if (lane == 0) M[k * na + k] = inv;
     __syncwarp();
   }
   // U -> D^-1 U: row i of the strict upper triangle times its pivot's reciprocal
 #pragma unroll 1
   for (int i = 0; i < na - 1; ++i) {
-    const double d = M[i * NS + i];
-    for (int c = i + 1 + lane; c < na; c += 32) M[i * NS + c] *= d;
+    const double d = M[i * na + i];
+    for (int c = i + 1 + lane; c < na; c += 32) M[i * na + c] *= d;
   }
   __syncwarp();
   return true;
@@ -606,13 +611,13 @@ __device__ void warp_solve(const Scratch& s, double (&b)[2], int na) {
 #pragma unroll 1
     for (int j = 0; j < na - 1; ++j) {
       const double vj = __shfl_sync(0xffffffffu, x[0], j);
-      if (i0 > j && i0 < na) x[0] = fma(-M[i0 * NS + j], vj, x[0]);
+      if (i0 > j && i0 < na) x[0] = fma(-M[i0 * na + j], vj, x[0]);
     }
-    if (i0 < na) x[0] *= M[i0 * NS + i0];
+    if (i0 < na) x[0] *= M[i0 * na + i0];
 #pragma unroll 1
     for (int j = na - 1; j >= 1; --j) {
       const double vj = __shfl_sync(0xffffffffu, x[0], j);
-      if (i0 < j) x[0] = fma(-M[i0 * NS + j], vj, x[0]);
+      if (i0 < j) x[0] = fma(-M[i0 * na + j], vj, x[0]);
     }
     b[0] = i0 < na ? x[0] : 0.0;
     b[1] = 0.0;
@@ -626,14 +631,14 @@ __device__ void warp_solve(const Scratch& s, double (&b)[2], int na) {
 #pragma unroll 1
   for (int j = 0; j < R - 1; ++j) {   // rows below j on both registers (all of the first)
     const double vj = __shfl_sync(0xffffffffu, x[1], j);
-    x[0] = fma(-M[f0 * NS + j], vj, x[0]);
-    if (f1 > j && f1 < R) x[1] = fma(-M[f1 * NS + j], vj, x[1]);
+    x[0] = fma(-M[f0 * na + j], vj, x[0]);
+    if (f1 > j && f1 < R) x[1] = fma(-M[f1 * na + j], vj, x[1]);
   }
 #pragma unroll 1
   for (int j = R - 1; j < na - 1; ++j) {   // rows below j only on the first register
     const double src = j < R ? x[1] : x[0];
     const double vj = __shfl_sync(0xffffffffu, src, j < R ? j : j - R);
-    if (f0 > j) x[0] = fma(-M[f0 * NS + j], vj, x[0]);
+    if (f0 > j) x[0] = fma(-M[f0 * na + j], vj, x[0]);
   }
   // to the backward layout through shared memory
   v[f0] = x[0];
@@ -642,19 +647,19 @@ __device__ void warp_solve(const Scratch& s, double (&b)[2], int na) {
   x[0] = v[i0];
   x[1] = i1 < na ? v[i1] : 0.0;
   __syncwarp();
-  x[0] *= M[i0 * NS + i0];
-  if (i1 < na) x[1] *= M[i1 * NS + i1];
+  x[0] *= M[i0 * na + i0];
+  if (i1 < na) x[1] *= M[i1 * na + i1];
 #pragma unroll 1
   for (int j = na - 1; j > 32; --j) {   // rows above j on both registers (all of the first)
     const double vj = __shfl_sync(0xffffffffu, x[1], j - 32);
-    x[0] = fma(-M[i0 * NS + j], vj, x[0]);
-    if (i1 < j) x[1] = fma(-M[i1 * NS + j], vj, x[1]);
+    x[0] = fma(-M[i0 * na + j], vj, x[0]);
+    if (i1 < j) x[1] = fma(-M[i1 * na + j], vj, x[1]);
   }
 #pragma unroll 1
   for (int j = 32; j >= 1; --j) {   // rows above j only on the first register (none above row 0)
     const double src = j < 32 ? x[0] : x[1];
     const double vj = __shfl_sync(0xffffffffu, src, j & 31);
-    if (i0 < j) x[0] = fma(-M[i0 * NS + j], vj, x[0]);
+    if (i0 < j) x[0] = fma(-M[i0 * na + j], vj, x[0]);
   }
   b[0] = x[0];
   b[1] = i1 < na ? x[1] : 0.0;
@@ -846,7 +851,7 @@ __global__ void __launch_bounds__(32 * kStiffWarpsMax, 1) stiff_kernel_lg(const 
   int* soff = reinterpret_cast<int*>(smem + pre);
   if (a.nbox > 0) stage_box_offsets(soff, a.box_off, a.nbox);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const ScratchLayout L = scratch_layout(NS, m.nr, m.ntb, true);
+  const ScratchLayout L = scratch_layout(NS, m.nr, m.ntb, true, m.mv.nact);
   const Scratch s = make_scratch(smem + pre + box_smem_bytes(a.nbox) + warp * L.bytes, L);
   const int qn = min(*reinterpret_cast<volatile int*>(&a.ws->qcount), static_cast<int>(a.n));
   CellCtx c;
@@ -910,7 +915,7 @@ __global__ void __launch_bounds__(32 * kStiffWarpsMax, 1) stiff_kernel_lg(const 
 #pragma unroll
         for (int kk = 0; kk < 2; ++kk) Yf[kk] = static_cast<float>(y[kk]);
         warp_jacobian<NS>(m, s, c.rho, static_cast<float>(Tc), Yf, cvR);
-        warp_iteration_matrix<NS>(s, gh);
+        warp_iteration_matrix<NS>(s, gh, m.mv.nact);
         conv = warp_lu<NS>(s, m.mv.nact);
         ++c_lu;
         lu_valid = conv;
@@ -1079,21 +1084,21 @@ static unsigned pad128(unsigned b) { return (b + 127u) & ~127u; }
 size_t bulk_smem_bytes_lg(int ns, int nr, int ntb, unsigned prefix, int nbox) {
   return pad128(prefix) + box_smem_bytes(nbox) + lg::kBulkWarps * lg::scratch_layout(ns, nr, ntb, false).bytes;
 }
-size_t stiff_smem_bytes_lg(int ns, int nr, int ntb, unsigned prefix, int nbox, int warps) {
-  return pad128(prefix) + box_smem_bytes(nbox) + warps * lg::scratch_layout(ns, nr, ntb, true).bytes;
+size_t stiff_smem_bytes_lg(int ns, int na, int nr, int ntb, unsigned prefix, int nbox, int warps) {
+  return pad128(prefix) + box_smem_bytes(nbox) + warps * lg::scratch_layout(ns, nr, ntb, true, na).bytes;
 }
 
 // Warps per CTA of the stiff kernel: as many per-warp scratch areas as fit next to the staged
 // tables in the device's opt-in shared memory per block (1 KB kept for the kernel's static shared
 // memory), between 1 and kStiffWarpsMax.
-static int stiff_warps_lg(int ns, int nr, int ntb, unsigned prefix, int nbox) {
+static int stiff_warps_lg(int ns, int na, int nr, int ntb, unsigned prefix, int nbox) {
   int dev = 0, optin = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
     return 1;
   const long long room = static_cast<long long>(optin) - 1024 -
-                         static_cast<long long>(stiff_smem_bytes_lg(ns, nr, ntb, prefix, nbox, 0));
-  const long long w = room / static_cast<long long>(lg::scratch_layout(ns, nr, ntb, true).bytes);
+                         static_cast<long long>(stiff_smem_bytes_lg(ns, na, nr, ntb, prefix, nbox, 0));
+  const long long w = room / static_cast<long long>(lg::scratch_layout(ns, nr, ntb, true, na).bytes);
   return w < 1 ? 1 : (w > lg::kStiffWarpsMax ? lg::kStiffWarpsMax : static_cast<int>(w));
 }
 
@@ -1111,11 +1116,11 @@ int launch_bulk_lg(int ns, int nr, int ntb, const AdvanceArgs<float>& a, int gri
   return -1;
 }
 
-int launch_stiff_lg(int ns, int nr, int ntb, const AdvanceArgs<float>& a, int grid, cudaStream_t s) {
+int launch_stiff_lg(int ns, int na, int nr, int ntb, const AdvanceArgs<float>& a, int grid, cudaStream_t s) {
 #define X(N)                                                                                     \
   if (ns == N) {                                                                                 \
-    const int w = stiff_warps_lg(N, nr, ntb, a.blob_bytes, a.nbox);                              \
-    const size_t smem = stiff_smem_bytes_lg(N, nr, ntb, a.blob_bytes, a.nbox, w);                \
+    const int w = stiff_warps_lg(N, na, nr, ntb, a.blob_bytes, a.nbox);                          \
+    const size_t smem = stiff_smem_bytes_lg(N, na, nr, ntb, a.blob_bytes, a.nbox, w);            \
     cudaFuncSetAttribute(lg::stiff_kernel_lg<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
                          static_cast<int>(smem));                                                \
     lg::stiff_kernel_lg<N><<<grid, 32 * w, smem, s>>>(a);                                        \
@@ -1145,12 +1150,12 @@ int launch_rates_lg(int ns, int nr, int ntb, const unsigned char* blob, unsigned
   return -1;
 }
 
-int occupancy_lg(int ns, int nr, int ntb, unsigned prefix, bool stiff, int* blocks_per_sm) {
+int occupancy_lg(int ns, int na, int nr, int ntb, unsigned prefix, bool stiff, int* blocks_per_sm) {
 #define X(N)                                                                                          \
   if (ns == N) {                                                                                      \
     if (stiff) {                                                                                      \
-      const int w = stiff_warps_lg(N, nr, ntb, prefix, 0);                                            \
-      const size_t smem = stiff_smem_bytes_lg(N, nr, ntb, prefix, 0, w);                              \
+      const int w = stiff_warps_lg(N, na, nr, ntb, prefix, 0);                                        \
+      const size_t smem = stiff_smem_bytes_lg(N, na, nr, ntb, prefix, 0, w);                          \
       cudaFuncSetAttribute(lg::stiff_kernel_lg<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,       \
                            static_cast<int>(smem));                                                   \
       return static_cast<int>(cudaOccupancyMaxActiveBlocksPerMultiprocessor(                          \

@@ -59,19 +59,23 @@ MechHdr layout(const chem_mechanism* m, bool large) {
   h.off_gam = off; off = align16(off + 4u * nreg * nr * 8);
   h.off_hco = off; off = align16(off + 4u * nreg * nr * 8);
   h.off_hsp = off; off = align16(off + 4u * 3 * ns * 8);
-  h.off_e64 = off; off = align16(off + 8u * 3 * ns * 8);
   if (!large) {
+    h.off_e64 = off; off = align16(off + 8u * 3 * ns * 8);
     h.off_arr64 = off; off = align16(off + 8u * 4 * nr);
     h.off_gam64 = off; off = align16(off + 8u * 3 * nr * 8);
     h.off_eff64 = off; off = align16(off + 8u * (ntb > 0 ? ntb : 1) * nsp);
     h.prefix = off;
   } else {
-    h.off_sto = off; off = align16(off + 8u * nr);
+    // staged: the species -> reaction index; global tail (read through L1): the per-reaction
+    // Gibbs / enthalpy coefficients, the FP64 thermo coefficients and the packed stoichiometry,
+    // so that the shared memory holds more cells of the stiff kernel
     h.off_cptr = off; off = align16(off + 4u * (ns + 1));
     h.off_cent = off; off = align16(off + 4u * nnz);
     h.prefix = off;
     h.off_gamg = off; off = align16(off + 4u * 3 * nr * 8);
     h.off_hcog = off; off = align16(off + 4u * 3 * nr * 8);
+    h.off_e64 = off; off = align16(off + 8u * 3 * ns * 8);
+    h.off_sto = off; off = align16(off + 8u * nr);
   }
   h.bytes = static_cast<int>(off);
   return h;
