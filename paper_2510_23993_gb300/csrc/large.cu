@@ -859,11 +859,21 @@ __global__ void __launch_bounds__(32 * kStiffWarpsMax, 1) stiff_kernel_lg(const 
   c.atol = a.prm.atol;
   unsigned long long c_sub = 0, c_fail = 0, c_att = 0, c_newt = 0, c_lu = 0;
   int flags = 0;
+  // every warp's first cell is queue position warp * gridDim.x + blockIdx.x (interleaved over
+  // the CTAs, so that a queue shorter than the warp slots, ordered most expensive first, spreads
+  // evenly over the SMs); later cells come from the shared counter, after those slots
+  const int slots = static_cast<int>(gridDim.x) * static_cast<int>(blockDim.x >> 5);
+  bool first = true;
 #pragma unroll 1
   while (true) {
     int q = 0;
-    if (lane == 0) q = atomicAdd(&a.ws->head, 1);
-    q = __shfl_sync(0xffffffffu, q, 0);
+    if (first) {
+      q = warp * static_cast<int>(gridDim.x) + static_cast<int>(blockIdx.x);
+      first = false;
+    } else {
+      if (lane == 0) q = slots + atomicAdd(&a.ws->head, 1);
+      q = __shfl_sync(0xffffffffu, q, 0);
+    }
     if (q >= qn) break;
     const int cell = a.queue[q];
     double dt, y[2], Tc;
