@@ -671,18 +671,23 @@ struct CellCtx {
 };
 
 // stage equation z = yb + hh f(z) by simplified Newton (as stage_newton in stiff.cu)
+// known_T: the start iterate z is the step's initial state and Tz its temperature (inverted at the
+// state tolerance), so the first iteration skips the inversion.
 template <int NS>
 __device__ bool warp_stage_newton(const LView& m, const Scratch& s, const CellCtx& c, const double (&yb)[2],
-                                  double hh, double (&z)[2], double& Tz, float& eta, unsigned long long& n_it) {
+                                  double hh, double (&z)[2], double& Tz, float& eta, unsigned long long& n_it,
+                                  bool known_T) {
   const int lane = threadIdx.x & 31;
   // the convergence control (norm, contraction rate) is FP32: it only decides when to stop
   float prev = 0.0f;
 #pragma unroll 1
   for (int it = 0; it < kNewtMax; ++it) {
     ++n_it;
-    bool ok;
-    Tz = warp_temperature<NS>(m, z, c.e0, Tz, &ok, nullptr, kTeIterateTol);
-    if (!ok) return false;
+    if (it > 0 || !known_T) {
+      bool ok;
+      Tz = warp_temperature<NS>(m, z, c.e0, Tz, &ok, nullptr, kTeIterateTol);
+      if (!ok) return false;
+    }
     float Zf[2], F[2];
 #pragma unroll
     for (int kk = 0; kk < 2; ++kk) Zf[kk] = static_cast<float>(z[kk]);
@@ -946,7 +951,7 @@ __global__ void __launch_bounds__(32 * kStiffWarpsMax, 1) stiff_kernel_lg(const 
           base[kk] = y[kk] + a1 * hk1[kk] + a2 * hk2[kk];
           z[kk] = y[kk] + p1 * hk1[kk] + p2 * hk2[kk];
         }
-        conv = warp_stage_newton<NS>(m, s, c, base, gh, z, Tz, eta, c_newt);
+        conv = warp_stage_newton<NS>(m, s, c, base, gh, z, Tz, eta, c_newt, st == 0);
         if (st < 2) {
 #pragma unroll
           for (int kk = 0; kk < 2; ++kk) {

@@ -193,19 +193,23 @@ struct CellCtx {
 // theta of the iteration: the iterate is accepted when the remaining error predicted from theta,
 // eta * |dz| with eta = theta / (1 - theta), is below kNewtTol.  eta carries over between the
 // stages of a step (the first iteration of a stage uses the last value).  it and prev hold the
-// stage's iteration count and last norm.  Returns 1 when the stage has converged, 0 to iterate
-// again, -1 on failure (T(e) lost, non-finite or diverging update, kNewtMax iterations).
+// stage's iteration count and last norm.  known_T: z is the step's initial state and Tz its
+// temperature (inverted at the state tolerance), so the iterate's inversion is skipped.  Returns
+// 1 when the stage has converged, 0 to iterate again, -1 on failure (T(e) lost, non-finite or
+// diverging update, kNewtMax iterations).
 template <class P>
 __device__ __forceinline__ int newton_iteration(const P& m, const Smem<P::NJ>& s, unsigned long long piv,
                                                 const CellCtx& c, const double (&yb)[P::NS], double hh,
                                                 double (&z)[P::NS], double& Tz, float& eta, float& prev, int& it,
-                                                unsigned long long& n_it) {
+                                                unsigned long long& n_it, bool known_T) {
   constexpr int NS = P::NS;
   ++n_it;
-  bool ok;
-  // FP64 rates (CHEM_FLAG_FP64_RATES) resolve T beyond FP32: their iterates keep the strict tolerance
-  Tz = m.temperature(z, c.e0, Tz, &ok, nullptr, c.fp64_rates ? kTeStateTol : kTeIterateTol);
-  if (!ok) return -1;
+  if (__builtin_expect(!known_T, 1)) {
+    bool ok;
+    // FP64 rates (CHEM_FLAG_FP64_RATES) resolve T beyond FP32: their iterates keep the strict tolerance
+    Tz = m.temperature(z, c.e0, Tz, &ok, nullptr, c.fp64_rates ? kTeStateTol : kTeIterateTol);
+    if (!ok) return -1;
+  }
   float F[NS], Zf[NS];
 #pragma unroll
   for (int k = 0; k < NS; ++k) Zf[k] = static_cast<float>(z[k]);
@@ -468,7 +472,8 @@ __device__ __forceinline__ void stiff_body(const AdvanceArgs<S>& a, const P& m, 
 #pragma unroll 1
     while (__any_sync(work, act)) {
       if (act) {
-        const int r = newton_iteration<P>(m, sm, piv, c, base, gh, z, Tz, eta, prev, it, c_newt);
+        // the first iterate of stage 1 is y itself, whose temperature Tc is known
+        const int r = newton_iteration<P>(m, sm, piv, c, base, gh, z, Tz, eta, prev, it, c_newt, st == 0 && it == 0);
         if (r < 0) {
           conv = false;
           act = false;
