@@ -50,7 +50,8 @@ N_EDGE = 128
 #       na x na block (sum_k 2 (na-k-1)^2 + (na-k-1), plus na reciprocals) + error filter
 #       (5 na + solve 2 na^2 + norm 2 na)
 #   per Newton iteration: T(e) (mixture 12 ns + 2 iterations x 21) + residual 3 na + solve 2 na^2
-#       + update/norm 2 na
+#       + update/norm 2 na, except that the first iteration of an attempt starts from the step's
+#       initial state, whose temperature is known: one T(e) fewer per attempt
 #   per accepted step: T(e) of the new state (12 ns + 42)
 
 
@@ -65,12 +66,17 @@ def f_attempt(ns, na):
     return f_factor(ns, na) + 5 * na + 2 * na * na + 2 * na
 
 
+def f_te(ns):
+    """One FP64 T(e) inversion: the mixture sums and two Newton iterations on the polynomial."""
+    return 12 * ns + 42
+
+
 def f_newton(ns, na):
-    return (12 * ns + 42) + 3 * na + 2 * na * na + 2 * na
+    return f_te(ns) + 3 * na + 2 * na * na + 2 * na
 
 
 def f_accept(ns, na):
-    return 12 * ns + 42
+    return f_te(ns)
 
 
 def active_species(mech):
@@ -310,7 +316,7 @@ def _stiff_flops(st, ns, na):
     """Algorithmic FP64 flops of the stiff phase from the counters of one advance call (the
     factorisations counted as done: the large-mechanism kernel reuses some across steps)."""
     nf = st.get("factorizations", st["attempts"])
-    return (st["attempts"] * (f_attempt(ns, na) - f_factor(ns, na)) + nf * f_factor(ns, na)
+    return (st["attempts"] * (f_attempt(ns, na) - f_factor(ns, na) - f_te(ns)) + nf * f_factor(ns, na)
             + st["newton"] * f_newton(ns, na) + st["substeps"] * f_accept(ns, na))
 
 
